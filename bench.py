@@ -1,0 +1,325 @@
+"""Benchmark of the FB-LTS hot path on GB300: cell-updates/s, % of HBM peak, latency.
+
+One step = one coarse FB-LTS step (coarse advancement, interface prediction,
+M fine subcycles with the correction sums, interface correction) of the whole
+synthetic workload, through the C ABI.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fblts|reference]
+                  [--workload shelf|bump] [--precision fp64|fp32]
+
+With N > 1 (torchrun) every rank advances its own replica of the workload
+(the method has no cross-replica exchange); value = all ranks' cell-updates
+divided by the slowest rank's time.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SWE cell-updates/s (% HBM peak), FP32 vs FP64 at stated err; p50/p99 latency"
+UNIT = "cell-updates/s"
+
+
+def make_workload(name):
+    from synth import scenario
+    if name == "shelf":
+        s = scenario.shelf_case()
+        desc = ("periodic-in-y 512x512 hex channel, dc 2 km, walls in x, tanh shelf 10-4000 m with 5% "
+                "roughness, 2 LTS levels (M=4) by gravity-wave CFL, 15 m/s wind stress + quadratic drag")
+    elif name == "bump":
+        s = scenario.gaussian_bump_case(two_level=True)
+        desc = "doubly periodic 32x32 hex, flat 1000 m, Gaussian bump, 2 LTS levels (M=2)"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return s, desc
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2405_10505_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(workload, precision, kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if current."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get(f"{workload}/{precision}/{kernel}")
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def oracle_sample(s, budget_s=15.0):
+    """Times the FP64 oracle on whole coarse steps of the workload (single thread)."""
+    import oracle
+    m = oracle.Mesh.from_scenario(s)
+    p = oracle.scenario_params(s)
+    h, u = s.h0.copy(), s.u0.copy()
+    n, t0 = 0, time.perf_counter()
+    while True:
+        h, u = oracle.fblts(m, p, s.level, s.M, h, u, s.dt, 1, t0=n * s.dt)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s or n >= 50:
+            break
+    el = time.perf_counter() - t0
+    return n, el, h, u
+
+
+def forcing_flags(s):
+    import paper_2405_10505_gb300 as fb
+    fz = s.forcing
+    return ((fb.FORCE_WIND_STRESS if fz.wind_stress else 0) | (fb.FORCE_BOTTOM_DRAG if fz.cd else 0)
+            | (fb.FORCE_VORTEX if fz.vortex is not None else 0))
+
+
+def cell_updates_per_step(s):
+    counts = np.bincount(s.level, minlength=s.nLevels)
+    mult, cu = 1, 0
+    for l in range(s.nLevels):
+        cu += int(counts[l]) * mult
+        if l + 1 < s.nLevels:
+            mult *= s.M[l]
+    return cu
+
+
+def run_reference(args, s, desc, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(s, budget_s=0.0)
+    cu = cell_updates_per_step(s)
+    times = []
+    for k in range(args.steps):
+        n, el, _, _ = oracle_sample(s, budget_s=0.0)
+        times.append(el / n)
+    ms = 1000.0 * statistics.mean(times)
+    v = cu / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "cells": int(s.mesh.nCells)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} whole coarse steps of {args.workload}, single-thread C oracle"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fblts", choices=["fblts", "reference"])
+    ap.add_argument("--workload", default="shelf")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    s, desc = make_workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, s, desc, rank)
+        return
+
+    import torch
+    import paper_2405_10505_gb300 as fb
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prec = fb.FP64 if args.precision == "fp64" else fb.FP32_TENDENCY
+    stream = torch.cuda.Stream()
+    mesh = fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M)
+    fz = s.forcing
+    vt = list(fz.vortex) + [float(np.mean(s.fVertex))] if fz.vortex is not None else None
+    params = fb.make_params(s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
+                            rho0=fz.rho0, rho_air=fz.rho_air, vortex=vt, precision=prec,
+                            stream=stream.cuda_stream, use_graph=True)
+    st = fb.state_init(mesh, params, s.h0, s.u0, s.bottom)
+    info = mesh.info()
+    cu = int(info.cell_updates_per_step)
+    launches = fb.launches_per_step(st)
+    step_bytes, _ = fb.state_step_bytes(st)
+
+    fb.lts_advance(st, args.warmup)
+    fb.synchronize(st)
+
+    # timed region: K coarse steps, one event per step for the latency percentiles
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for k in range(args.steps):
+            fb.lts_advance(st, 1)
+            evs[k + 1].record(stream)
+        fb.synchronize(st)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms_total = evs[0].elapsed_time(evs[-1])
+    lat = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * cu * args.steps / (ms_total / 1000.0)
+
+    # per-kernel profile (launch by launch with events on the same stream)
+    prof = fb.state_profile_step(st)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dms, dn, dbytes = prof[dom]
+    hbm, peak_src = peaks()
+    achieved = dbytes / (dms / 1000.0) / 1e9
+    kernel_name = {"cell": "cell_pass", "vertex": "vert_pass", "edge_prep": "eprep_pass",
+                   "edge": "edge_pass"}.get(dom, dom)
+    traffic = traffic_for(args.workload, args.precision, kernel_name)
+
+    # end to end through the public host-buffer call: H2D inputs, 1 step, D2H result
+    nC, nE = info.nCells, info.nEdges
+    hin = torch.empty(nC, dtype=torch.float64, pin_memory=True).numpy()
+    uin = torch.empty(nE, dtype=torch.float64, pin_memory=True).numpy()
+    hout = torch.empty(nC, dtype=torch.float64, pin_memory=True).numpy()
+    uout = torch.empty(nE, dtype=torch.float64, pin_memory=True).numpy()
+    fb.state_read(st, hin, uin)
+    n_e2e = max(3, min(args.steps, 20))
+    fb.run_host(st, hin, uin, 1, hout, uout)
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        fb.run_host(st, hin, uin, 1, hout, uout)
+    e2e_s = time.perf_counter() - t0
+    e2e_v = world * cu * n_e2e / e2e_s
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == fb.FP64 else "f32-tendency/f64-state",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "cells": nC, "edges": nE,
+                   "vertices": int(info.nVertices), "levels": int(info.nLevels), "M": list(s.M),
+                   "cells_per_level": [int(x) for x in list(info.cells_per_level)[: info.nLevels]],
+                   "cell_updates_per_step": cu, "precision": args.precision,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"inputs larger than L2: {step_bytes / 1e6:.0f} MB algorithmic traffic per step"},
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "alg_bytes_per_step": step_bytes,
+        "alg_bytes_per_cell_update": step_bytes / cu,
+        "step_hbm_frac": step_bytes / (ms_step / 1000.0) / 1e9 / hbm,
+        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
+                     "launches_per_step": dn, "share_of_step": dms / sum(v[0] for v in prof.values())},
+        "profile_ms_per_step": {k: round(v[0], 4) for k, v in prof.items()},
+        "gpu_launches": int(launches * args.steps + 1),
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 8 * (nC + nE),
+                "d2h_bytes_per_step": 8 * (nC + nE), "steps": n_e2e},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fb.state_write(st, s.h0, s.u0)
+        n, el, ho, uo = oracle_sample(s)
+        line["cpu_baseline"] = {"value": cu * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n} whole coarse steps of the same workload, single-thread C oracle",
+                                "host_cores_available": os.cpu_count()}
+        # error of this run against the oracle on the same window
+        st2 = fb.state_init(mesh, params, s.h0, s.u0, s.bottom)
+        fb.lts_advance(st2, n)
+        h, u = fb.state_read(st2)
+        line["err_vs_oracle"] = {"coarse_steps": n, "h_rel_max": float(np.max(np.abs(h - ho) / np.abs(ho))),
+                                 "u_rel_max": float(np.max(np.abs(u - uo)) / max(np.max(np.abs(uo)), 1e-300))}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

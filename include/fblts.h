@@ -1,0 +1,265 @@
+/*
+ * fblts.h - C ABI of the GB300 FB-LTS shallow-water library.
+ *
+ * What it computes (Lilly et al., "Local Time-Stepping for the Shallow Water
+ * Equations using CFL Optimized Forward-Backward Runge-Kutta Schemes"):
+ *   - the TRiSK tendencies of the rotating shallow-water equations on an
+ *     unstructured Voronoi C-grid [Sec. 2.2, Eq. nonlinear_swe, Eq.
+ *     semi_discrete_sys]: thickness-flux divergence [Eq. trisk_thickness],
+ *     vertex potential vorticity and the nonlinear Coriolis term q F_perp
+ *     [Eq. trisk_vorticity], kinetic-energy and pressure gradients, and the
+ *     wind-stress / bottom-drag / surface-pressure forcing of Eq.
+ *     hurricane_model;
+ *   - advanced by FB-RK(3,2) [Sec. 2.1, Eq. fbrk32] inside the FB-LTS scheme
+ *     [Sec. 2.2]: coarse advancement, interface prediction [Eq. preds,
+ *     Eq. hstar_preds], M fine subcycles [Eq. fine_fbrk32] and interface
+ *     correction [Eq. if_correction].  More than two levels are handled by
+ *     nesting: each fine subcycle of a level pair is an FB-LTS step of the
+ *     next pair.
+ *
+ * Conventions common to every call:
+ *   - Every function returns an fblts_status; none aborts, traps or exits.
+ *     On failure fblts_last_error() returns a message (thread-local).
+ *   - Index arrays are 0-based int32, -1 = absent.  Real arrays are double.
+ *   - Host arrays passed in are read during the call only; the library keeps
+ *     its own copies (the caller keeps ownership).  Arrays handed out are
+ *     always in the caller's original cell / edge order.
+ *   - A handle may be used from one host thread at a time.
+ *   - Device work is issued on the stream given in fblts_params (or the
+ *     library's own stream) and is asynchronous unless a function says it
+ *     synchronises.
+ */
+#ifndef FBLTS_H
+#define FBLTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fblts_status {
+    FBLTS_OK = 0,
+    FBLTS_E_ARG = 1,      /* bad argument (NULL, size, range, inconsistent counts) */
+    FBLTS_E_MESH = 2,     /* connectivity or metrics invalid */
+    FBLTS_E_REGIONS = 3,  /* LTS levels cannot form the required interface bands */
+    FBLTS_E_OOM = 4,      /* host or device allocation failed */
+    FBLTS_E_CUDA = 5,     /* a CUDA call failed (message carries the CUDA error) */
+    FBLTS_E_UNSTABLE = 6, /* the state became non-finite or a thickness <= 0 */
+    FBLTS_E_TIMEOUT = 7,  /* a bounded device wait gave up */
+    FBLTS_E_STATE = 8     /* handle in the wrong state (e.g. checkpoint mismatch) */
+} fblts_status;
+
+typedef struct fblts_mesh fblts_mesh;
+typedef struct fblts_state fblts_state;
+
+/* Thread-local text of the last error; never NULL. */
+const char *fblts_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Mesh                                                                    */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * MPAS-style mesh description (Sec. 2.2, Fig. trisk).  Sizes: nC cells,
+ * nE edges, nV vertices (dual triangles, vertexDegree = 3).
+ *
+ *  cellsOnEdge[nE*2]      (c0, c1); the edge normal n_e points from c0 to c1;
+ *                         one entry -1 marks a no-flow boundary edge (u = 0).
+ *  nEdgesOnCell[nC], edgesOnCell[nC*maxEdges]  edges of each cell (any order).
+ *  verticesOnEdge[nE*2]   (v0, v1) ordered so that t_e = k x n_e points from
+ *                         v0 to v1 (then t_{e,v0} = -1, t_{e,v1} = +1 in
+ *                         Eq. trisk_vorticity).
+ *  cellsOnVertex[nV*3]    cells around each vertex (-1 = absent/land).
+ *  edgesOnVertex[nV*3]    edges around each vertex; may be NULL (derived).
+ *  nEdgesOnEdge[nE], edgesOnEdge[nE*maxEdges2], weightsOnEdge[nE*maxEdges2]
+ *                         TRiSK tangential reconstruction: the tangential
+ *                         thickness flux is F_perp_e = sum_j w_j F_{e_j}
+ *                         (the dv/dc metric factor is included in w).
+ *  dcEdge[nE]             distance between the two cell centres (d_e).
+ *  dvEdge[nE]             length of the primal edge (l_e).
+ *  areaCell[nC]           A_i.
+ *  kiteAreasOnVertex[nV*3] kite of cellsOnVertex[v][j] at v; A_v is the sum
+ *                         of the kites of the present cells.
+ *  fVertex[nV]            Coriolis parameter at vertices.
+ *  angleEdge[nE]          direction of n_e (radians from +x); needed only for
+ *                         wind forcing (may be NULL otherwise).
+ *  xCell,yCell[nC]        optional; used for the space-filling-curve order
+ *                         and the moving vortex forcing.
+ *  xEdge,yEdge[nE]        optional; needed for the vortex forcing.
+ *  ltsLevel[nC]           LTS level per cell, 0 = coarsest; NULL = all 0.
+ *  nLevels                number of levels (>= 1); every level must be
+ *                         populated.
+ *  M[nLevels-1]           M[l] = dt_l / dt_{l+1} (positive integers).
+ *  nIF1Layers, nIF2Layers cell layers of the IF-1 / IF-2 bands (0 = 2, the
+ *                         stencil radius of TRiSK, Sec. 2.2).
+ *
+ * Layout rules checked by fblts_mesh_create (FBLTS_E_REGIONS otherwise):
+ * level l cells adjacent only to levels l-1, l, l+1, and for three or more
+ * levels every level l-1 cell at least 10 + nIF1 + nIF2 + 3 cell layers (17
+ * with the default bands) from every level >= l+1 cell, so that the F^5 band
+ * of one level pair and the interface bands of the next stay disjoint.
+ */
+typedef struct fblts_mesh_desc {
+    int32_t nCells, nEdges, nVertices, maxEdges, maxEdges2;
+    const int32_t *cellsOnEdge;
+    const int32_t *nEdgesOnCell;
+    const int32_t *edgesOnCell;
+    const int32_t *verticesOnEdge;
+    const int32_t *cellsOnVertex;
+    const int32_t *edgesOnVertex;
+    const int32_t *nEdgesOnEdge;
+    const int32_t *edgesOnEdge;
+    const double *weightsOnEdge;
+    const double *dcEdge;
+    const double *dvEdge;
+    const double *areaCell;
+    const double *kiteAreasOnVertex;
+    const double *fVertex;
+    const double *angleEdge;
+    const double *xCell, *yCell;
+    const double *xEdge, *yEdge;
+    const int32_t *ltsLevel;
+    int32_t nLevels;
+    const int32_t *M;
+    int32_t nIF1Layers, nIF2Layers;
+} fblts_mesh_desc;
+
+/* Validates, classifies the LTS regions (Sec. 2.2: F, F^1..F^5, IF-1, IF-2,
+ * interior, edge ownership "closest to the fine region"), renumbers cells,
+ * edges and vertices so that every region is one contiguous range, and
+ * uploads the metadata to the current CUDA device.  *out receives the handle. */
+fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mesh **out);
+fblts_status fblts_mesh_destroy(fblts_mesh *mesh);
+
+/* Counts derived by fblts_mesh_create (host only, no device work). */
+typedef struct fblts_mesh_info {
+    int32_t nCells, nEdges, nVertices, nLevels;
+    int64_t cells_per_level[8];
+    /* cell-updates per coarse step: sum_l N_l * prod_{m<l} M_m */
+    int64_t cell_updates_per_step;
+    /* fine-level cell updates of FB-LTS done on IF-1/IF-2 and F^l bands */
+    int64_t band_cells[8];
+} fblts_mesh_info;
+fblts_status fblts_mesh_get_info(const fblts_mesh *mesh, fblts_mesh_info *info);
+
+/* ---------------------------------------------------------------------- */
+/* State                                                                   */
+/* ---------------------------------------------------------------------- */
+
+enum { FBLTS_FP64 = 0, FBLTS_FP32_TENDENCY = 1 };
+enum {
+    FBLTS_FORCE_WIND_STRESS = 1, /* C_W |u_W - u| (u_W - u) / h, Eq. hurricane_model */
+    FBLTS_FORCE_BOTTOM_DRAG = 2, /* -C_D |u| u / h */
+    FBLTS_FORCE_VORTEX = 4       /* moving Holland vortex: wind + surface pressure */
+};
+
+/*
+ * Run parameters.
+ *  g             gravitational acceleration (m s^-2).
+ *  dt            coarse time step (s) of level 0.
+ *  beta[3]       FB weights of Eq. fbrk32 (the paper uses 0.531, 0.531, 0.313).
+ *  precision     FBLTS_FP64: all arithmetic in double.  FBLTS_FP32_TENDENCY:
+ *                tendencies and stage intermediates in float; time levels,
+ *                correction sums and diagnostics in double.
+ *  forcing       FBLTS_FORCE_* bits.  Wind and pressure are evaluated at the
+ *                start of each coarse step and held for its stages and
+ *                subcycles; drag follows the state.
+ *  wind_u,wind_v uniform wind (m s^-1) added to the vortex wind.
+ *  cd            bottom-drag coefficient C_D.
+ *  rho0,rho_air  water and air density (kg m^-3); the wind-stress
+ *                coefficient is C_W = rho_air/rho0 (0.75 + 0.067 |u_W|) 1e-3.
+ *  vortex[9]     pc, dp, rmax, B, x0, y0, vx, vy, f0: pressure
+ *                p = pc + dp exp(-(rmax/r)^B) around the centre
+ *                (x0 + vx t, y0 + vy t), gradient wind with Coriolis f0.
+ *  t0            time of the initial state (s).
+ *  stream        cudaStream_t to issue work on, or NULL for an own stream.
+ *  use_graph     non-zero: capture one coarse step as a CUDA graph.
+ */
+typedef struct fblts_params {
+    double g;
+    double dt;
+    double beta[3];
+    int32_t precision;
+    int32_t forcing;
+    double wind_u, wind_v;
+    double cd;
+    double rho0, rho_air;
+    double vortex[9];
+    double t0;
+    void *stream;
+    int32_t use_graph;
+} fblts_params;
+
+/* Allocates the device state (one arena), uploads h0[nC], u0[nE] and the
+ * bottom b[nC] = -H (caller order).  u0 on no-flow edges is forced to 0. */
+fblts_status fblts_state_init(const fblts_mesh *mesh, const fblts_params *params,
+                              const double *h0, const double *u0, const double *bottom,
+                              fblts_state **out);
+fblts_status fblts_state_destroy(fblts_state *state);
+
+/* Advances n coarse steps (asynchronous).  A non-finite value or h <= 0
+ * found by the end-of-call check is reported as FBLTS_E_UNSTABLE by the next
+ * synchronising call. */
+fblts_status fblts_lts_advance(fblts_state *state, int64_t n_coarse_steps);
+
+/* Blocks until the state's device work is done; reports FBLTS_E_UNSTABLE. */
+fblts_status fblts_synchronize(fblts_state *state);
+
+/* Copies the state to host arrays h_out[nC], u_out[nE] (caller order; either
+ * may be NULL).  Synchronises. */
+fblts_status fblts_state_read(const fblts_state *state, double *h_out, double *u_out);
+
+/* Replaces the state from host arrays h[nC], u[nE] (caller order); either may
+ * be NULL to keep that field.  Copies are issued on the state's stream. */
+fblts_status fblts_state_write(fblts_state *state, const double *h, const double *u);
+
+/* End-to-end call for host callers: uploads h_in/u_in, advances n coarse
+ * steps and downloads the result to h_out/u_out (all caller order, host
+ * memory; pinned memory makes the copies faster).  Synchronises. */
+fblts_status fblts_run_host(fblts_state *state, const double *h_in, const double *u_in,
+                            int64_t n_coarse_steps, double *h_out, double *u_out);
+
+/* Total mass sum_i A_i h_i and total absolute vorticity sum_v A_v (zeta_v + f_v)
+ * (Sec. 2.3), reduced on the device in a fixed order (deterministic).
+ * Synchronises. */
+fblts_status fblts_diagnostics(const fblts_state *state, double *total_mass,
+                               double *total_abs_vorticity);
+
+/* Coarse steps done and the current time. */
+fblts_status fblts_state_time(const fblts_state *state, int64_t *steps, double *time);
+
+/* Checkpoint: serialises (step, time, h, u) to buf.  With buf == NULL only
+ * *len is set to the size needed.  Synchronises. */
+fblts_status fblts_state_save(const fblts_state *state, void *buf, size_t *len);
+/* Restores a checkpoint written by fblts_state_save for the same mesh. */
+fblts_status fblts_state_load(fblts_state *state, const void *buf, size_t len);
+
+/* Launch statistics of one coarse step: kernels launched per step. */
+fblts_status fblts_state_launches_per_step(const fblts_state *state, int64_t *launches);
+
+/* Per-kernel profile of one coarse step: the step is issued launch by launch
+ * (no graph) with a CUDA event pair around each launch on the state's
+ * stream; it advances the state by one step like fblts_lts_advance(state, 1).
+ * For each kind k (FBLTS_PK_*), ms[k] is the summed device time, launches[k]
+ * the launch count and alg_bytes[k] the algorithmic bytes: every array element
+ * the launch's arithmetic must read or write, counted once at its storage
+ * size (metadata included).  Arrays have FBLTS_PROFILE_KINDS entries; any may
+ * be NULL.  Synchronises. */
+enum {
+    FBLTS_PK_CELL = 0, FBLTS_PK_VERTEX, FBLTS_PK_EDGE_PREP, FBLTS_PK_EDGE, FBLTS_PK_SAVE,
+    FBLTS_PK_PREDICT, FBLTS_PK_CORRECT, FBLTS_PK_FORCING, FBLTS_PK_STEP_END, FBLTS_PROFILE_KINDS
+};
+fblts_status fblts_state_profile_step(fblts_state *state, double *ms, int64_t *launches,
+                                      double *alg_bytes);
+
+/* Algorithmic bytes of one coarse step (sum over its launches, same model as
+ * fblts_state_profile_step) and cell-updates per step. */
+fblts_status fblts_state_step_bytes(const fblts_state *state, double *alg_bytes,
+                                    int64_t *cell_updates);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBLTS_H */

@@ -1,0 +1,329 @@
+"""Python binding of the GB300 FB-LTS library (include/fblts.h).
+
+Argument marshalling only: every step of the time integration runs in the
+CUDA library ``_build/libfblts.so`` (built by :mod:`.build` for sm_103a).  There
+is no CPU fallback: if the library cannot be built or loaded, every call
+raises.
+
+The functions carry the names of the C entry points without the ``fblts_``
+prefix; handles are opaque ``ctypes`` pointers wrapped in :class:`Mesh` and
+:class:`State`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, E_ARG, E_MESH, E_REGIONS, E_OOM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE = range(9)
+FP64, FP32_TENDENCY = 0, 1
+FORCE_WIND_STRESS, FORCE_BOTTOM_DRAG, FORCE_VORTEX = 1, 2, 4
+PAPER_BETA = (0.531, 0.531, 0.313)   # Sec. 2.1, CFL-optimised FB weights
+
+_PI = C.POINTER(C.c_int32)
+_PD = C.POINTER(C.c_double)
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("nCells", C.c_int32), ("nEdges", C.c_int32), ("nVertices", C.c_int32),
+                ("maxEdges", C.c_int32), ("maxEdges2", C.c_int32),
+                ("cellsOnEdge", _PI), ("nEdgesOnCell", _PI), ("edgesOnCell", _PI),
+                ("verticesOnEdge", _PI), ("cellsOnVertex", _PI), ("edgesOnVertex", _PI),
+                ("nEdgesOnEdge", _PI), ("edgesOnEdge", _PI), ("weightsOnEdge", _PD),
+                ("dcEdge", _PD), ("dvEdge", _PD), ("areaCell", _PD), ("kiteAreasOnVertex", _PD),
+                ("fVertex", _PD), ("angleEdge", _PD), ("xCell", _PD), ("yCell", _PD),
+                ("xEdge", _PD), ("yEdge", _PD), ("ltsLevel", _PI), ("nLevels", C.c_int32),
+                ("M", _PI), ("nIF1Layers", C.c_int32), ("nIF2Layers", C.c_int32)]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("nCells", C.c_int32), ("nEdges", C.c_int32), ("nVertices", C.c_int32),
+                ("nLevels", C.c_int32), ("cells_per_level", C.c_int64 * 8),
+                ("cell_updates_per_step", C.c_int64), ("band_cells", C.c_int64 * 8)]
+
+
+class Params(C.Structure):
+    _fields_ = [("g", C.c_double), ("dt", C.c_double), ("beta", C.c_double * 3),
+                ("precision", C.c_int32), ("forcing", C.c_int32), ("wind_u", C.c_double),
+                ("wind_v", C.c_double), ("cd", C.c_double), ("rho0", C.c_double),
+                ("rho_air", C.c_double), ("vortex", C.c_double * 9), ("t0", C.c_double),
+                ("stream", C.c_void_p), ("use_graph", C.c_int32)]
+
+
+class FbltsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fblts status {status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts_mesh_get_info",
+           "fblts_state_init", "fblts_state_destroy", "fblts_lts_advance", "fblts_synchronize",
+           "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
+           "fblts_state_time", "fblts_state_save", "fblts_state_load", "fblts_state_launches_per_step",
+           "fblts_state_profile_step", "fblts_state_step_bytes")
+PROFILE_KINDS = ("cell", "vertex", "edge_prep", "edge", "save", "predict", "correct", "forcing", "step_end")
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if stale) the CUDA library; raises if impossible."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = C.CDLL(path)
+        L.fblts_last_error.restype = C.c_char_p
+        V = C.c_void_p
+        sig = {
+            "fblts_mesh_create": [C.POINTER(MeshDesc), C.POINTER(V)],
+            "fblts_mesh_destroy": [V],
+            "fblts_mesh_get_info": [V, C.POINTER(MeshInfo)],
+            "fblts_state_init": [V, C.POINTER(Params), _PD, _PD, _PD, C.POINTER(V)],
+            "fblts_state_destroy": [V],
+            "fblts_lts_advance": [V, C.c_int64],
+            "fblts_synchronize": [V],
+            "fblts_state_read": [V, _PD, _PD],
+            "fblts_state_write": [V, _PD, _PD],
+            "fblts_run_host": [V, _PD, _PD, C.c_int64, _PD, _PD],
+            "fblts_diagnostics": [V, _PD, _PD],
+            "fblts_state_time": [V, C.POINTER(C.c_int64), _PD],
+            "fblts_state_save": [V, V, C.POINTER(C.c_size_t)],
+            "fblts_state_load": [V, V, C.c_size_t],
+            "fblts_state_launches_per_step": [V, C.POINTER(C.c_int64)],
+            "fblts_state_profile_step": [V, _PD, C.POINTER(C.c_int64), _PD],
+            "fblts_state_step_bytes": [V, _PD, C.POINTER(C.c_int64)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        _LIB = L
+    return _LIB
+
+
+def last_error():
+    return lib().fblts_last_error().decode()
+
+
+def _check(status):
+    if status != OK:
+        raise FbltsError(status, last_error())
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a, t):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+class Mesh:
+    """Handle of a created mesh (owns the device metadata)."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def info(self):
+        return mesh_get_info(self)
+
+    def close(self):
+        if self.handle:
+            mesh_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """Handle of a device state; keeps its mesh alive."""
+
+    def __init__(self, handle, mesh):
+        self.handle = handle
+        self.mesh = mesh
+
+    def close(self):
+        if self.handle:
+            state_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mesh_create(m, fVertex, level=None, M=None, nIF1=0, nIF2=0):
+    """fblts_mesh_create from MPAS-named arrays on ``m`` (any object with those attributes)."""
+    keep = {}
+
+    def I(name, arr=None):
+        a = _i32(getattr(m, name) if arr is None else arr)
+        keep[name] = a
+        return _p(a, _PI)
+
+    def D(name, arr=None, optional=False):
+        src = getattr(m, name, None) if arr is None else arr
+        if src is None:
+            if optional:
+                return None
+            raise ValueError(f"mesh array {name} missing")
+        a = _f64(src)
+        keep[name] = a
+        return _p(a, _PD)
+
+    nL = 1
+    lev_p = M_p = None
+    if level is not None:
+        lev = _i32(level)
+        nL = int(lev.max()) + 1 if lev.size else 1
+        keep["level"] = lev
+        lev_p = _p(lev, _PI)
+        Ma = _i32(list(M or []) + [1])
+        keep["M"] = Ma
+        M_p = _p(Ma, _PI)
+    eov = getattr(m, "edgesOnVertex", None)
+    d = MeshDesc(int(m.nCells), int(m.nEdges), int(m.nVertices), int(m.maxEdges), int(m.maxEdges2),
+                 I("cellsOnEdge"), I("nEdgesOnCell"), I("edgesOnCell"), I("verticesOnEdge"),
+                 I("cellsOnVertex"), I("edgesOnVertex") if eov is not None else None,
+                 I("nEdgesOnEdge"), I("edgesOnEdge"), D("weightsOnEdge"), D("dcEdge"), D("dvEdge"),
+                 D("areaCell"), D("kiteAreasOnVertex"), D("fVertex", fVertex),
+                 D("angleEdge", optional=True), D("xCell", optional=True), D("yCell", optional=True),
+                 D("xEdge", optional=True), D("yEdge", optional=True), lev_p, nL, M_p, int(nIF1), int(nIF2))
+    keep["desc"] = d
+    h = C.c_void_p()
+    _check(lib().fblts_mesh_create(C.byref(d), C.byref(h)))
+    return Mesh(h, keep)
+
+
+def mesh_destroy(mesh):
+    h, mesh.handle = mesh.handle, None
+    if h:
+        _check(lib().fblts_mesh_destroy(h))
+
+
+def mesh_get_info(mesh):
+    info = MeshInfo()
+    _check(lib().fblts_mesh_get_info(mesh.handle, C.byref(info)))
+    return info
+
+
+def make_params(dt, g=9.80616, beta=PAPER_BETA, precision=FP64, forcing=0, wind=(0.0, 0.0), cd=0.0,
+                rho0=1025.0, rho_air=1.225, vortex=None, t0=0.0, stream=None, use_graph=True):
+    p = Params()
+    p.g, p.dt = g, dt
+    p.beta[:] = list(beta)
+    p.precision, p.forcing = precision, forcing
+    p.wind_u, p.wind_v = wind
+    p.cd, p.rho0, p.rho_air = cd, rho0, rho_air
+    if vortex is not None:
+        p.vortex[:] = list(vortex)
+    p.t0 = t0
+    p.stream = stream
+    p.use_graph = int(bool(use_graph))
+    return p
+
+
+def state_init(mesh, params, h0, u0, bottom):
+    h0, u0, bottom = _f64(h0), _f64(u0), _f64(bottom)
+    h = C.c_void_p()
+    _check(lib().fblts_state_init(mesh.handle, C.byref(params), _p(h0, _PD), _p(u0, _PD), _p(bottom, _PD),
+                                  C.byref(h)))
+    return State(h, mesh)
+
+
+def state_destroy(state):
+    h, state.handle = state.handle, None
+    if h:
+        _check(lib().fblts_state_destroy(h))
+
+
+def lts_advance(state, n):
+    _check(lib().fblts_lts_advance(state.handle, int(n)))
+
+
+def synchronize(state):
+    _check(lib().fblts_synchronize(state.handle))
+
+
+def state_read(state, h_out=None, u_out=None):
+    info = state.mesh.info()
+    h = np.empty(info.nCells) if h_out is None else h_out
+    u = np.empty(info.nEdges) if u_out is None else u_out
+    _check(lib().fblts_state_read(state.handle, _p(h, _PD), _p(u, _PD)))
+    return h, u
+
+
+def state_write(state, h=None, u=None):
+    h = None if h is None else _f64(h)
+    u = None if u is None else _f64(u)
+    _check(lib().fblts_state_write(state.handle, _p(h, _PD), _p(u, _PD)))
+
+
+def run_host(state, h_in, u_in, n, h_out, u_out):
+    """End-to-end call on host buffers (numpy arrays, ideally pinned)."""
+    _check(lib().fblts_run_host(state.handle, _p(h_in, _PD), _p(u_in, _PD), int(n), _p(h_out, _PD),
+                                _p(u_out, _PD)))
+
+
+def diagnostics(state):
+    a, b = C.c_double(), C.c_double()
+    _check(lib().fblts_diagnostics(state.handle, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def state_time(state):
+    n, t = C.c_int64(), C.c_double()
+    _check(lib().fblts_state_time(state.handle, C.byref(n), C.byref(t)))
+    return n.value, t.value
+
+
+def state_save(state):
+    n = C.c_size_t(0)
+    _check(lib().fblts_state_save(state.handle, None, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(lib().fblts_state_save(state.handle, buf, C.byref(n)))
+    return bytes(buf.raw[: n.value])
+
+
+def state_load(state, blob):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(lib().fblts_state_load(state.handle, buf, len(blob)))
+
+
+def launches_per_step(state):
+    n = C.c_int64()
+    _check(lib().fblts_state_launches_per_step(state.handle, C.byref(n)))
+    return n.value
+
+
+def state_profile_step(state):
+    """Per-kind (ms, launches, algorithmic bytes) of one coarse step, issued launch by launch."""
+    k = len(PROFILE_KINDS)
+    ms = (C.c_double * k)()
+    nl = (C.c_int64 * k)()
+    by = (C.c_double * k)()
+    _check(lib().fblts_state_profile_step(state.handle, ms, nl, by))
+    return {PROFILE_KINDS[i]: (ms[i], nl[i], by[i]) for i in range(k)}
+
+
+def state_step_bytes(state):
+    b, cu = C.c_double(), C.c_int64()
+    _check(lib().fblts_state_step_bytes(state.handle, C.byref(b), C.byref(cu)))
+    return b.value, cu.value

@@ -1,0 +1,585 @@
+// C ABI of the FB-LTS library (include/fblts.h): handles, device arenas,
+// the captured coarse step, caller-order I/O, diagnostics and checkpoints.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace fblts {
+
+namespace {
+thread_local char g_err[1024] = "no error";
+}
+
+const char *last_error_text() { return g_err; }
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+bool arr_is_cell(int a) {
+    switch (a) {
+        case A_H: case A_HS1: case A_HS2: case A_HS3: case A_HST1: case A_HST2: case A_HST3:
+        case A_K: case A_ACCH: case A_SH0: case A_SH1: case A_SH2: case A_SH3: return true;
+        default: return false;
+    }
+}
+bool arr_is_vert(int a) { return a == A_Q; }
+
+namespace {
+
+// Bump allocator over one device allocation.
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+    size_t reserve(size_t bytes) {  // sizing pass
+        used = ((used + 255) & ~size_t(255)) + bytes;
+        return used;
+    }
+    void *take(size_t bytes) {
+        size_t off = (used + 255) & ~size_t(255);
+        if (off + bytes > size) return nullptr;
+        used = off + bytes;
+        return base + off;
+    }
+};
+
+// slot-major copy of a row-major [n][k] table
+template <class T>
+std::vector<T> slot_major(const std::vector<T> &v, int n, int k) {
+    std::vector<T> out((size_t)n * k);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < k; ++j) out[(size_t)j * n + i] = v[(size_t)i * k + j];
+    return out;
+}
+
+}  // namespace
+}  // namespace fblts
+
+using namespace fblts;
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t err__ = (call);                                                         \
+        if (err__ != cudaSuccess) {                                                         \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(err__), __FILE__,  \
+                      __LINE__);                                                            \
+            return err__ == cudaErrorMemoryAllocation ? FBLTS_E_OOM : FBLTS_E_CUDA;         \
+        }                                                                                   \
+    } while (0)
+
+struct fblts_mesh {
+    HostMesh hm;
+    int device = 0;
+    void *dbase = nullptr;
+    DevMesh dm{};
+    int *cell_n2o = nullptr, *cell_o2n = nullptr, *edge_n2o = nullptr, *edge_o2n = nullptr;
+};
+
+struct fblts_state {
+    const fblts_mesh *mesh = nullptr;
+    fblts_params p{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    void *dbase = nullptr;
+    DevArrays arr{};
+    DevMesh dm{};
+    DevForcing fz{};
+    long long *d_step = nullptr;
+    int *d_flag = nullptr;
+    double *d_partials = nullptr, *d_diag = nullptr;
+    double *d_stage_c = nullptr, *d_stage_e = nullptr;
+    Schedule sched;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t steps = 0;
+};
+
+extern "C" const char *fblts_last_error(void) { return last_error_text(); }
+
+// ------------------------------------------------------------------ mesh
+
+extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mesh **out) {
+    if (!out) { set_error("mesh_create: out is NULL"); return FBLTS_E_ARG; }
+    *out = nullptr;
+    fblts_mesh *m = new (std::nothrow) fblts_mesh();
+    if (!m) { set_error("mesh_create: host allocation failed"); return FBLTS_E_OOM; }
+    fblts_status s = build_host_mesh(desc, m->hm);
+    if (s != FBLTS_OK) { delete m; return s; }
+    const HostMesh &hm = m->hm;
+    const int nC = hm.nC, nE = hm.nE, nV = hm.nV, mE = hm.maxE, mE2 = hm.maxE2;
+    if (cudaGetDevice(&m->device) != cudaSuccess) {
+        set_error("mesh_create: no CUDA device (%s)", cudaGetErrorString(cudaGetLastError()));
+        delete m;
+        return FBLTS_E_CUDA;
+    }
+    // host staging of every device array, then one allocation and one copy
+    struct Item { const void *src; size_t bytes; void **dst; };
+    std::vector<Item> items;
+    std::vector<std::vector<int>> ikeep;
+    std::vector<std::vector<double>> dkeep;
+    std::vector<std::vector<unsigned char>> bkeep;
+    DevMesh &dm = m->dm;
+    dm.nC = nC; dm.nE = nE; dm.nV = nV; dm.maxE = mE; dm.maxE2 = mE2;
+    auto addi = [&](std::vector<int> v, const int **dst) {
+        ikeep.push_back(std::move(v));
+        items.push_back({ikeep.back().data(), ikeep.back().size() * sizeof(int), (void **)dst});
+    };
+    auto addd = [&](std::vector<double> v, const double **dst) {
+        dkeep.push_back(std::move(v));
+        items.push_back({dkeep.back().data(), dkeep.back().size() * sizeof(double), (void **)dst});
+    };
+    ikeep.reserve(32); dkeep.reserve(32); bkeep.reserve(2);
+    addi(hm.nEoC, &dm.nEoC);
+    addi(slot_major(hm.eoc, nC, mE), &dm.eoc);
+    addi(slot_major(hm.coc, nC, mE), &dm.coc);
+    addd(slot_major(hm.cDiv, nC, mE), &dm.cDiv);
+    addd(slot_major(hm.cKE, nC, mE), &dm.cKE);
+    addd(hm.area, &dm.area);
+    std::vector<int> c0(nE), c1(nE), v0(nE), v1(nE);
+    for (int e = 0; e < nE; ++e) { c0[e] = hm.coe[2 * e]; c1[e] = hm.coe[2 * e + 1]; v0[e] = hm.voe[2 * e]; v1[e] = hm.voe[2 * e + 1]; }
+    addi(c0, &dm.coe0); addi(c1, &dm.coe1); addi(v0, &dm.voe0); addi(v1, &dm.voe1);
+    addi(hm.nEoE, &dm.nEoE);
+    addi(slot_major(hm.eoe, nE, mE2), &dm.eoe);
+    addd(slot_major(hm.woe, nE, mE2), &dm.woe);
+    addd(hm.invDc, &dm.invDc);
+    bkeep.push_back(hm.ebnd);
+    items.push_back({bkeep.back().data(), bkeep.back().size(), (void **)&dm.ebnd});
+    addd(hm.cosE, &dm.cosE); addd(hm.sinE, &dm.sinE); addd(hm.xE, &dm.xE); addd(hm.yE, &dm.yE);
+    addd(hm.xC, &dm.xC); addd(hm.yC, &dm.yC);
+    addi(slot_major(hm.eov, nV, 3), &dm.eov);
+    addi(slot_major(hm.cov, nV, 3), &dm.cov);
+    addd(slot_major(hm.cVort, nV, 3), &dm.cVort);
+    addd(slot_major(hm.cKite, nV, 3), &dm.cKite);
+    addd(hm.fV, &dm.fV);
+    addd(hm.Av, &dm.Av);
+    addi(hm.cell_n2o, (const int **)&m->cell_n2o);
+    addi(hm.cell_o2n, (const int **)&m->cell_o2n);
+    addi(hm.edge_n2o, (const int **)&m->edge_n2o);
+    addi(hm.edge_o2n, (const int **)&m->edge_o2n);
+    Arena ar;
+    for (auto &it : items) ar.reserve(it.bytes);
+    ar.size = ar.used + 256;
+    if (cudaMalloc(&m->dbase, ar.size) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("mesh_create: cudaMalloc of %zu bytes failed", ar.size);
+        delete m;
+        return FBLTS_E_OOM;
+    }
+    ar.base = (char *)m->dbase;
+    ar.used = 0;
+    std::vector<char> host(ar.size, 0);
+    for (auto &it : items) {
+        char *d = (char *)ar.take(it.bytes);
+        std::memcpy(host.data() + (d - ar.base), it.src, it.bytes);
+        *it.dst = d;
+    }
+    if (cudaMemcpy(m->dbase, host.data(), ar.size, cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("mesh_create: upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        cudaFree(m->dbase);
+        delete m;
+        return FBLTS_E_CUDA;
+    }
+    dm.bottom = nullptr;
+    *out = m;
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_mesh_destroy(fblts_mesh *m) {
+    if (!m) return FBLTS_OK;
+    if (m->dbase) cudaFree(m->dbase);
+    delete m;
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_mesh_get_info(const fblts_mesh *m, fblts_mesh_info *info) {
+    if (!m || !info) { set_error("mesh_get_info: NULL argument"); return FBLTS_E_ARG; }
+    std::memset(info, 0, sizeof(*info));
+    const HostMesh &hm = m->hm;
+    info->nCells = hm.nC; info->nEdges = hm.nE; info->nVertices = hm.nV; info->nLevels = hm.L;
+    for (int l = 0; l < hm.L && l < 8; ++l) info->cells_per_level[l] = hm.cells_per_level[l];
+    info->cell_updates_per_step = hm.cell_updates_per_step;
+    // band sizes: IF-1 u IF-2 cells of each level pair
+    for (int l = 0; l + 1 < hm.L && l < 8; ++l) {
+        uint32_t k0 = BandKey::make(hm.L, l, 0, 0);
+        int b0 = hm.cell_lb(k0);
+        int b1 = hm.cell_lb(BandKey::make(hm.L, l, hm.nIF1 + hm.nIF2 + 1, 0));
+        info->band_cells[l] = b1 - b0;
+    }
+    return FBLTS_OK;
+}
+
+// ------------------------------------------------------------------ state
+
+static fblts_status capture_graph(fblts_state *s);
+
+static fblts_status issue_step(fblts_state *s) {
+    if (s->gexec) {
+        CK(cudaGraphLaunch(s->gexec, s->st));
+        return FBLTS_OK;
+    }
+    for (const Op &op : s->sched.ops) CK(launch_op(op, s->dm, s->arr, s->fz, s->p.g, s->d_step, s->st));
+    return FBLTS_OK;
+}
+
+static fblts_status capture_graph(fblts_state *s) {
+    CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    for (const Op &op : s->sched.ops) {
+        cudaError_t e = launch_op(op, s->dm, s->arr, s->fz, s->p.g, s->d_step, s->st);
+        if (e != cudaSuccess) {
+            cudaGraph_t g;
+            cudaStreamEndCapture(s->st, &g);
+            if (g) cudaGraphDestroy(g);
+            set_error("graph capture: %s", cudaGetErrorString(e));
+            return FBLTS_E_CUDA;
+        }
+    }
+    CK(cudaStreamEndCapture(s->st, &s->graph));
+    CK(cudaGraphInstantiate(&s->gexec, s->graph, 0));
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_state_destroy(fblts_state *s) {
+    if (!s) return FBLTS_OK;
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->st) cudaStreamSynchronize(s->st);
+    if (s->dbase) cudaFree(s->dbase);
+    if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+    delete s;
+    return FBLTS_OK;
+}
+
+static fblts_status upload_state(fblts_state *s, const double *h, const double *u) {
+    const fblts_mesh *m = s->mesh;
+    const int nC = m->hm.nC, nE = m->hm.nE;
+    if (h) {
+        CK(cudaMemcpyAsync(s->d_stage_c, h, sizeof(double) * nC, cudaMemcpyHostToDevice, s->st));
+        CK(launch_gather(s->arr.a[A_H], s->d_stage_c, m->cell_n2o, nC, s->st));
+    }
+    if (u) {
+        CK(cudaMemcpyAsync(s->d_stage_e, u, sizeof(double) * nE, cudaMemcpyHostToDevice, s->st));
+        CK(launch_gather(s->arr.a[A_U], s->d_stage_e, m->edge_n2o, nE, s->st));
+        CK(launch_zero_boundary(s->arr.a[A_U], s->dm.ebnd, nE, s->st));
+    }
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params *p, const double *h0,
+                                         const double *u0, const double *bottom, fblts_state **out) {
+    if (!out) { set_error("state_init: out is NULL"); return FBLTS_E_ARG; }
+    *out = nullptr;
+    if (!m || !p || !h0 || !u0 || !bottom) { set_error("state_init: NULL argument"); return FBLTS_E_ARG; }
+    if (!(p->dt > 0.0) || !(p->g > 0.0)) { set_error("state_init: dt and g must be positive"); return FBLTS_E_ARG; }
+    if (p->precision != FBLTS_FP64 && p->precision != FBLTS_FP32_TENDENCY) {
+        set_error("state_init: unknown precision %d", p->precision);
+        return FBLTS_E_ARG;
+    }
+    if (p->precision == FBLTS_FP32_TENDENCY) {
+        set_error("state_init: FBLTS_FP32_TENDENCY is not available in this build");
+        return FBLTS_E_ARG;
+    }
+    if ((p->forcing & FBLTS_FORCE_WIND_STRESS) && !m->hm.has_angle) {
+        set_error("state_init: wind forcing needs angleEdge in the mesh");
+        return FBLTS_E_ARG;
+    }
+    if ((p->forcing & FBLTS_FORCE_VORTEX) && !(m->hm.has_xy_cell && m->hm.has_xy_edge && m->hm.has_angle)) {
+        set_error("state_init: vortex forcing needs xCell/yCell/xEdge/yEdge/angleEdge");
+        return FBLTS_E_ARG;
+    }
+    if (p->forcing & ~7) { set_error("state_init: unknown forcing bits"); return FBLTS_E_ARG; }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev != m->device) { set_error("state_init: current device differs from the mesh's"); return FBLTS_E_ARG; }
+    fblts_state *s = new (std::nothrow) fblts_state();
+    if (!s) { set_error("state_init: host allocation failed"); return FBLTS_E_OOM; }
+    s->mesh = m;
+    s->p = *p;
+    const HostMesh &hm = m->hm;
+    const int nC = hm.nC, nE = hm.nE, nV = hm.nV;
+    if (p->stream) {
+        s->st = (cudaStream_t)p->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+            set_error("state_init: stream creation failed");
+            delete s;
+            return FBLTS_E_CUDA;
+        }
+        s->own_stream = true;
+    }
+    // arena layout
+    Arena ar;
+    size_t szc = sizeof(double) * (size_t)nC, sze = sizeof(double) * (size_t)nE, szv = sizeof(double) * (size_t)nV;
+    for (int a = 0; a < A_COUNT; ++a) ar.reserve(arr_is_cell(a) ? szc : (arr_is_vert(a) ? szv : sze));
+    ar.reserve(szc);                      // bottom
+    ar.reserve(sze * 3 + szc);            // forcing
+    ar.reserve(64);                       // step + flag
+    ar.reserve(sizeof(double) * (2 * DIAG_BLOCKS + 2));
+    ar.reserve(szc); ar.reserve(sze);     // staging
+    ar.size = ar.used + 256;
+    if (cudaMalloc(&s->dbase, ar.size) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("state_init: cudaMalloc of %zu bytes failed", ar.size);
+        fblts_state_destroy(s);
+        return FBLTS_E_OOM;
+    }
+    ar.base = (char *)s->dbase;
+    ar.used = 0;
+    for (int a = 0; a < A_COUNT; ++a)
+        s->arr.a[a] = (double *)ar.take(arr_is_cell(a) ? szc : (arr_is_vert(a) ? szv : sze));
+    double *db = (double *)ar.take(szc);
+    s->fz.windN = (double *)ar.take(sze);
+    s->fz.windT = (double *)ar.take(sze);
+    s->fz.cw = (double *)ar.take(sze);
+    s->fz.ps = (double *)ar.take(szc);
+    s->d_step = (long long *)ar.take(64);
+    s->d_flag = (int *)((char *)s->d_step + 16);
+    s->d_partials = (double *)ar.take(sizeof(double) * (2 * DIAG_BLOCKS + 2));
+    s->d_diag = s->d_partials + 2 * DIAG_BLOCKS;
+    s->d_stage_c = (double *)ar.take(szc);
+    s->d_stage_e = (double *)ar.take(sze);
+    if (cudaMemsetAsync(s->dbase, 0, ar.size, s->st) != cudaSuccess) {
+        set_error("state_init: memset failed");
+        fblts_state_destroy(s);
+        return FBLTS_E_CUDA;
+    }
+    s->dm = m->dm;
+    s->dm.bottom = db;
+    fblts_status st = upload_state(s, h0, u0);
+    if (st == FBLTS_OK) {
+        if (cudaMemcpyAsync(s->d_stage_c, bottom, szc, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+            launch_gather(db, s->d_stage_c, m->cell_n2o, nC, s->st) != cudaSuccess) {
+            set_error("state_init: bottom upload failed");
+            st = FBLTS_E_CUDA;
+        }
+    }
+    if (st != FBLTS_OK) { fblts_state_destroy(s); return st; }
+    DevForcing &fz = s->fz;
+    fz.flags = p->forcing;
+    fz.wind_u = p->wind_u; fz.wind_v = p->wind_v; fz.cd = p->cd;
+    fz.rho0 = p->rho0 > 0 ? p->rho0 : 1025.0;
+    fz.rho_air = p->rho_air > 0 ? p->rho_air : 1.225;
+    for (int k = 0; k < 9; ++k) fz.vx[k] = p->vortex[k];
+    fz.t0 = p->t0; fz.dt = p->dt; fz.step = s->d_step;
+    build_schedule(hm, p->dt, p->beta, s->sched);
+    schedule_bytes(hm, p->forcing, s->sched);
+    if (cudaStreamSynchronize(s->st) != cudaSuccess) {
+        set_error("state_init: %s", cudaGetErrorString(cudaGetLastError()));
+        fblts_state_destroy(s);
+        return FBLTS_E_CUDA;
+    }
+    if (p->use_graph) {
+        st = capture_graph(s);
+        if (st != FBLTS_OK) { fblts_state_destroy(s); return st; }
+    }
+    *out = s;
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_lts_advance(fblts_state *s, int64_t n) {
+    if (!s || n < 0) { set_error("lts_advance: bad arguments"); return FBLTS_E_ARG; }
+    for (int64_t i = 0; i < n; ++i) {
+        fblts_status st = issue_step(s);
+        if (st != FBLTS_OK) return st;
+    }
+    if (n > 0) CK(launch_check(s->arr.a[A_H], s->mesh->hm.nC, s->arr.a[A_U], s->mesh->hm.nE, s->d_flag, s->st));
+    s->steps += n;
+    return FBLTS_OK;
+}
+
+static fblts_status sync_and_check(const fblts_state *s) {
+    CK(cudaStreamSynchronize(s->st));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, s->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        set_error("state became non-finite or a thickness is <= 0");
+        return FBLTS_E_UNSTABLE;
+    }
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_synchronize(fblts_state *s) {
+    if (!s) { set_error("synchronize: NULL state"); return FBLTS_E_ARG; }
+    return sync_and_check(s);
+}
+
+extern "C" fblts_status fblts_state_read(const fblts_state *s, double *h_out, double *u_out) {
+    if (!s) { set_error("state_read: NULL state"); return FBLTS_E_ARG; }
+    const fblts_mesh *m = s->mesh;
+    const int nC = m->hm.nC, nE = m->hm.nE;
+    if (h_out) {
+        CK(launch_gather(s->d_stage_c, s->arr.a[A_H], m->cell_o2n, nC, s->st));
+        CK(cudaMemcpyAsync(h_out, s->d_stage_c, sizeof(double) * nC, cudaMemcpyDeviceToHost, s->st));
+    }
+    if (u_out) {
+        CK(launch_gather(s->d_stage_e, s->arr.a[A_U], m->edge_o2n, nE, s->st));
+        CK(cudaMemcpyAsync(u_out, s->d_stage_e, sizeof(double) * nE, cudaMemcpyDeviceToHost, s->st));
+    }
+    return sync_and_check(s);
+}
+
+extern "C" fblts_status fblts_state_write(fblts_state *s, const double *h, const double *u) {
+    if (!s) { set_error("state_write: NULL state"); return FBLTS_E_ARG; }
+    return upload_state(s, h, u);
+}
+
+extern "C" fblts_status fblts_run_host(fblts_state *s, const double *h_in, const double *u_in, int64_t n,
+                                       double *h_out, double *u_out) {
+    if (!s) { set_error("run_host: NULL state"); return FBLTS_E_ARG; }
+    fblts_status st = upload_state(s, h_in, u_in);
+    if (st != FBLTS_OK) return st;
+    st = fblts_lts_advance(s, n);
+    if (st != FBLTS_OK) return st;
+    return fblts_state_read(s, h_out, u_out);
+}
+
+extern "C" fblts_status fblts_diagnostics(const fblts_state *s, double *mass, double *absvort) {
+    if (!s) { set_error("diagnostics: NULL state"); return FBLTS_E_ARG; }
+    CK(launch_diagnostics(s->dm, s->arr.a[A_H], s->arr.a[A_U], s->d_partials, DIAG_BLOCKS, s->d_diag, s->st));
+    double out[2];
+    CK(cudaMemcpyAsync(out, s->d_diag, sizeof(out), cudaMemcpyDeviceToHost, s->st));
+    fblts_status st = sync_and_check(s);
+    if (mass) *mass = out[0];
+    if (absvort) *absvort = out[1];
+    return st;
+}
+
+extern "C" fblts_status fblts_state_time(const fblts_state *s, int64_t *steps, double *time) {
+    if (!s) { set_error("state_time: NULL state"); return FBLTS_E_ARG; }
+    if (steps) *steps = s->steps;
+    if (time) *time = s->p.t0 + (double)s->steps * s->p.dt;
+    return FBLTS_OK;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int64_t nC, nE, steps;
+    double t0, dt;
+};
+}  // namespace
+
+extern "C" fblts_status fblts_state_save(const fblts_state *s, void *buf, size_t *len) {
+    if (!s || !len) { set_error("state_save: NULL argument"); return FBLTS_E_ARG; }
+    const int nC = s->mesh->hm.nC, nE = s->mesh->hm.nE;
+    size_t need = sizeof(CkptHeader) + sizeof(double) * ((size_t)nC + nE);
+    if (!buf) { *len = need; return FBLTS_OK; }
+    if (*len < need) { set_error("state_save: buffer of %zu bytes, need %zu", *len, need); return FBLTS_E_ARG; }
+    CkptHeader hd;
+    std::memcpy(hd.magic, "FBLTSCK1", 8);
+    hd.nC = nC; hd.nE = nE; hd.steps = s->steps; hd.t0 = s->p.t0; hd.dt = s->p.dt;
+    std::memcpy(buf, &hd, sizeof(hd));
+    double *h = (double *)((char *)buf + sizeof(hd));
+    fblts_status st = fblts_state_read(s, h, h + nC);
+    *len = need;
+    return st;
+}
+
+extern "C" fblts_status fblts_state_load(fblts_state *s, const void *buf, size_t len) {
+    if (!s || !buf) { set_error("state_load: NULL argument"); return FBLTS_E_ARG; }
+    const int nC = s->mesh->hm.nC, nE = s->mesh->hm.nE;
+    CkptHeader hd;
+    if (len < sizeof(hd)) { set_error("state_load: buffer too small"); return FBLTS_E_STATE; }
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "FBLTSCK1", 8) != 0 || hd.nC != nC || hd.nE != nE ||
+        len < sizeof(hd) + sizeof(double) * ((size_t)nC + nE)) {
+        set_error("state_load: checkpoint does not match this mesh");
+        return FBLTS_E_STATE;
+    }
+    const double *h = (const double *)((const char *)buf + sizeof(hd));
+    fblts_status st = upload_state(s, h, h + nC);
+    if (st != FBLTS_OK) return st;
+    long long step = hd.steps;
+    CK(cudaMemcpyAsync(s->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    s->steps = hd.steps;
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_state_launches_per_step(const fblts_state *s, int64_t *launches) {
+    if (!s || !launches) { set_error("launches_per_step: NULL argument"); return FBLTS_E_ARG; }
+    int64_t n = 0;
+    for (const Op &op : s->sched.ops) {
+        if (op.kind == OP_FORCING && !s->fz.flags) continue;
+        if ((op.kind == OP_CELL || op.kind == OP_VERT || op.kind == OP_EPREP || op.kind == OP_EDGE) && op.hi <= op.lo)
+            continue;
+        n++;
+    }
+    *launches = n;
+    return FBLTS_OK;
+}
+
+static int op_kind_profile(int kind) {
+    switch (kind) {
+        case OP_CELL: return FBLTS_PK_CELL;
+        case OP_VERT: return FBLTS_PK_VERTEX;
+        case OP_EPREP: return FBLTS_PK_EDGE_PREP;
+        case OP_EDGE: return FBLTS_PK_EDGE;
+        case OP_SAVE: return FBLTS_PK_SAVE;
+        case OP_PRED: return FBLTS_PK_PREDICT;
+        case OP_FINAL: return FBLTS_PK_CORRECT;
+        case OP_FORCING: return FBLTS_PK_FORCING;
+        default: return FBLTS_PK_STEP_END;
+    }
+}
+
+extern "C" fblts_status fblts_state_profile_step(fblts_state *s, double *ms, int64_t *launches, double *bytes) {
+    if (!s) { set_error("profile_step: NULL state"); return FBLTS_E_ARG; }
+    const size_t n = s->sched.ops.size();
+    std::vector<cudaEvent_t> ev(2 * n, nullptr);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    fblts_status st = FBLTS_OK;
+    for (size_t i = 0; i < n && st == FBLTS_OK; ++i) {
+        const Op &op = s->sched.ops[i];
+        cudaError_t e1 = cudaEventRecord(ev[2 * i], s->st);
+        cudaError_t e2 = launch_op(op, s->dm, s->arr, s->fz, s->p.g, s->d_step, s->st);
+        cudaError_t e3 = cudaEventRecord(ev[2 * i + 1], s->st);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            set_error("profile_step: launch failed: %s", cudaGetErrorString(e2 != cudaSuccess ? e2 : (e1 != cudaSuccess ? e1 : e3)));
+            st = FBLTS_E_CUDA;
+        }
+    }
+    if (st == FBLTS_OK && cudaStreamSynchronize(s->st) != cudaSuccess) {
+        set_error("profile_step: %s", cudaGetErrorString(cudaGetLastError()));
+        st = FBLTS_E_CUDA;
+    }
+    double tms[FBLTS_PROFILE_KINDS] = {0}, tb[FBLTS_PROFILE_KINDS] = {0};
+    int64_t tl[FBLTS_PROFILE_KINDS] = {0};
+    for (size_t i = 0; i < n && st == FBLTS_OK; ++i) {
+        const Op &op = s->sched.ops[i];
+        bool empty = (op.kind == OP_FORCING && !s->fz.flags) ||
+                     ((op.kind == OP_CELL || op.kind == OP_VERT || op.kind == OP_EPREP || op.kind == OP_EDGE) &&
+                      op.hi <= op.lo);
+        if (empty) continue;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+        int k = op_kind_profile(op.kind);
+        tms[k] += t;
+        tl[k] += 1;
+        tb[k] += op.alg_bytes;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st != FBLTS_OK) return st;
+    s->steps += 1;
+    for (int k = 0; k < FBLTS_PROFILE_KINDS; ++k) {
+        if (ms) ms[k] = tms[k];
+        if (launches) launches[k] = tl[k];
+        if (bytes) bytes[k] = tb[k];
+    }
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_state_step_bytes(const fblts_state *s, double *bytes, int64_t *cell_updates) {
+    if (!s) { set_error("step_bytes: NULL state"); return FBLTS_E_ARG; }
+    double b = 0.0;
+    for (const Op &op : s->sched.ops) b += op.alg_bytes;
+    if (bytes) *bytes = b;
+    if (cell_updates) *cell_updates = s->mesh->hm.cell_updates_per_step;
+    return FBLTS_OK;
+}

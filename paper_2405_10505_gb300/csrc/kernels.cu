@@ -1,0 +1,194 @@
+// sm_103a kernels of the FB-LTS hot path.
+//
+// One thread per cell / vertex / edge of a contiguous band range; the mode of
+// each index (stage update, in-place update, correction sum, kinetic energy
+// only) comes from the launch's segment list.  The passes use no atomics, so
+// every result is bit-reproducible run to run.
+#include "kernel_bodies.cuh"
+
+namespace fblts {
+
+namespace {
+
+constexpr int TPB = 256;
+
+__global__ void __launch_bounds__(TPB) cell_pass(DevMesh m, CellArgs a) {
+    const int i = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.hi) cell_body(m, a, i);
+}
+
+__global__ void __launch_bounds__(TPB) vert_pass(DevMesh m, VertArgs a) {
+    const int v = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < a.hi) vert_body(m, a, v);
+}
+
+__global__ void __launch_bounds__(TPB) eprep_pass(DevMesh m, PrepArgs a) {
+    const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < a.hi) prep_body(m, a, e);
+}
+
+template <bool FORCING>
+__global__ void __launch_bounds__(TPB) edge_pass(DevMesh m, EdgeArgs a, DevForcing fz) {
+    const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < a.hi) edge_body<FORCING>(m, a, fz, e);
+}
+
+__global__ void __launch_bounds__(TPB) save_pass(IfArgs a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n) save_body(a, t);
+}
+
+__global__ void __launch_bounds__(TPB) pred_pass(IfArgs a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n) pred_body(a, t);
+}
+
+__global__ void __launch_bounds__(TPB) final_pass(IfArgs a, const unsigned char *ebnd) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n) final_body(a, ebnd, t);
+}
+
+__global__ void __launch_bounds__(TPB) forcing_pass(DevMesh m, DevForcing fz) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const double time = fz.t0 + (double)(*fz.step) * fz.dt;
+    forcing_body(m, fz, time, t);
+}
+
+__global__ void step_end(long long *step) { *step += 1; }
+
+__global__ void gather_kernel(double *dst, const double *src, const int *idx, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+__global__ void zero_bnd_kernel(double *u, const unsigned char *ebnd, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && ebnd[i]) u[i] = 0.0;
+}
+
+__device__ double block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+// Fixed-order partial sums (deterministic): thread t of the grid sums
+// elements t, t + G, t + 2G, ...; each block reduces with a fixed tree.
+__global__ void __launch_bounds__(TPB) diag_partials(DevMesh m, const double *h, const double *u,
+                                                      double *partials) {
+    __shared__ double sh[TPB];
+    const int G = gridDim.x * blockDim.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double mass = 0.0, vort = 0.0;
+    for (int i = t; i < m.nC; i += G) mass += m.area[i] * h[i];
+    const int nV = m.nV;
+    for (int v = t; v < nV; v += G) {
+        double c = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) c += m.cVort[j * nV + v] * u[m.eov[j * nV + v]];
+        vort += m.Av[v] * (c + m.fV[v]);
+    }
+    const double bm = block_sum(mass, sh);
+    __syncthreads();
+    const double bv = block_sum(vort, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = bm;
+        partials[2 * blockIdx.x + 1] = bv;
+    }
+}
+
+__global__ void __launch_bounds__(TPB) diag_final(const double *partials, int nb, double *out2) {
+    __shared__ double sh[TPB];
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        a += partials[2 * k];
+        b += partials[2 * k + 1];
+    }
+    const double sa = block_sum(a, sh);
+    __syncthreads();
+    const double sb = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        out2[0] = sa;
+        out2[1] = sb;
+    }
+}
+
+__global__ void check_kernel(const double *h, int nC, const double *u, int nE, int *flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (i < nC) bad |= !(h[i] > 0.0) || !isfinite(h[i]);
+    if (i < nE) bad |= !isfinite(u[i]);
+    if (bad) atomicOr(flag, 1);
+}
+
+inline int nblk(long long n) { return (int)((n + TPB - 1) / TPB); }
+
+}  // namespace
+
+cudaError_t launch_op(const Op &op, const DevMesh &m, const DevArrays &arr, const DevForcing &fz, double g,
+                      long long *step_counter, cudaStream_t st) {
+    switch (op.kind) {
+        case OP_CELL:
+            if (op.hi <= op.lo) return cudaSuccess;
+            cell_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, cell_args(op, arr));
+            break;
+        case OP_VERT:
+            if (op.hi <= op.lo) return cudaSuccess;
+            vert_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, vert_args(op, arr));
+            break;
+        case OP_EPREP:
+            if (op.hi <= op.lo) return cudaSuccess;
+            eprep_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, prep_args(op, arr));
+            break;
+        case OP_EDGE:
+            if (op.hi <= op.lo) return cudaSuccess;
+            if (fz.flags) edge_pass<true><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, edge_args(op, arr, g), fz);
+            else edge_pass<false><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, edge_args(op, arr, g), fz);
+            break;
+        case OP_SAVE:
+        case OP_PRED:
+        case OP_FINAL: {
+            IfArgs a = if_args(op, arr);
+            if (a.n <= 0) return cudaSuccess;
+            if (op.kind == OP_SAVE) save_pass<<<nblk(a.n), TPB, 0, st>>>(a);
+            else if (op.kind == OP_PRED) pred_pass<<<nblk(a.n), TPB, 0, st>>>(a);
+            else final_pass<<<nblk(a.n), TPB, 0, st>>>(a, m.ebnd);
+        } break;
+        case OP_FORCING:
+            if (!fz.flags) return cudaSuccess;
+            forcing_pass<<<nblk(m.nE > m.nC ? m.nE : m.nC), TPB, 0, st>>>(m, fz);
+            break;
+        case OP_STEP_END: step_end<<<1, 1, 0, st>>>(step_counter); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(double *dst, const double *src, const int *idx, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    gather_kernel<<<nblk(n), TPB, 0, st>>>(dst, src, idx, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_boundary(double *u, const unsigned char *ebnd, int nE, cudaStream_t st) {
+    zero_bnd_kernel<<<nblk(nE), TPB, 0, st>>>(u, ebnd, nE);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const DevMesh &m, const double *h, const double *u, double *partials, int nblocks,
+                               double *out2, cudaStream_t st) {
+    diag_partials<<<nblocks, TPB, 0, st>>>(m, h, u, partials);
+    diag_final<<<1, TPB, 0, st>>>(partials, nblocks, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check(const double *h, int nC, const double *u, int nE, int *flag, cudaStream_t st) {
+    check_kernel<<<nblk(nE > nC ? nE : nC), TPB, 0, st>>>(h, nC, u, nE, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace fblts

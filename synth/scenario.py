@@ -107,7 +107,7 @@ def graph_distance(mesh, seed_mask):
     return dist
 
 
-def enforce_level_separation(mesh, level, min_sep=7, max_iter=50):
+def enforce_level_separation(mesh, level, min_sep=17, max_iter=50):
     """Promote cells so that levels l-1 and l+1 are >= ``min_sep`` layers apart.
 
     A level-(l-1) cell closer than ``min_sep`` to a level >= l+1 cell is

@@ -1,0 +1,149 @@
+"""GPU FP64 path against the oracle, through the C ABI.
+
+Bar (from the method's accuracy target): after the stated number of coarse
+steps, max_i |dh_i|/|h_i| <= 1e-10 and max_e |du_e| / max_e |u_e| <= 1e-10,
+mass drift per step <= 1e-13 relative, bit-reproducible runs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2405_10505_gb300 as fb
+from synth import scenario
+from tests.gpu_util import make_state, rel_errors
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def _oracle(s, nsteps, M=None, level=None):
+    m = oracle.Mesh.from_scenario(s)
+    p = oracle.scenario_params(s)
+    return oracle.fblts(m, p, s.level if level is None else level, s.M if M is None else M,
+                        s.h0, s.u0, s.dt, nsteps)
+
+
+CASES = {
+    "bump_single": (lambda: scenario.gaussian_bump_case(two_level=False), 100, None),
+    "bump_lts_m2": (lambda: scenario.gaussian_bump_case(two_level=True), 100, None),
+    "bump_lts_m1": (lambda: scenario.gaussian_bump_case(two_level=True), 30, [1]),
+    "bump_lts_m5": (lambda: scenario.gaussian_bump_case(two_level=True), 30, [5]),
+    "shelf_forced_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3), 100, None),
+    "nested_3level": (lambda: scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3)), 40, None),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_parity_with_oracle(name):
+    make, nsteps, M = CASES[name]
+    s = make()
+    st = make_state(s, M=M)
+    fb.lts_advance(st, nsteps)
+    h, u = fb.state_read(st)
+    ho, uo = _oracle(s, nsteps, M=M)
+    dh, du = rel_errors(h, u, ho, uo)
+    assert dh <= TOL and du <= TOL, (dh, du)
+
+
+def test_graph_and_stream_launches_agree_bitwise():
+    s = scenario.gaussian_bump_case(two_level=True)
+    a = make_state(s, use_graph=True)
+    b = make_state(s, use_graph=False)
+    fb.lts_advance(a, 25)
+    fb.lts_advance(b, 25)
+    ha, ua = fb.state_read(a)
+    hb, ub = fb.state_read(b)
+    assert np.array_equal(ha, hb) and np.array_equal(ua, ub)
+
+
+def test_bit_reproducible():
+    s = scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3)
+    out = []
+    for _ in range(2):
+        st = make_state(s)
+        fb.lts_advance(st, 40)
+        out.append(fb.state_read(st))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_mass_drift_per_step_and_diagnostics():
+    s = scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3)
+    st = make_state(s)
+    m = oracle.Mesh.from_scenario(s)
+    mass0, av0 = fb.diagnostics(st)
+    om0, oa0 = oracle.diagnostics(m, s.h0, s.u0)
+    assert mass0 == pytest.approx(om0, rel=1e-13)
+    assert av0 == pytest.approx(oa0, rel=1e-12)
+    prev = mass0
+    for _ in range(10):
+        fb.lts_advance(st, 1)
+        cur, _ = fb.diagnostics(st)
+        assert abs(cur - prev) <= 1e-13 * mass0
+        prev = cur
+    h, u = fb.state_read(st)
+    om, oa = oracle.diagnostics(m, h, u)
+    gm, ga = fb.diagnostics(st)
+    assert gm == pytest.approx(om, rel=1e-13)
+    assert ga == pytest.approx(oa, rel=1e-12)
+
+
+def test_checkpoint_resume_is_bit_identical():
+    s = scenario.gaussian_bump_case(two_level=True)
+    a = make_state(s)
+    fb.lts_advance(a, 30)
+    ref_h, ref_u = fb.state_read(a)
+    b = make_state(s)
+    fb.lts_advance(b, 12)
+    blob = fb.state_save(b)
+    c = make_state(s)
+    fb.state_load(c, blob)
+    assert fb.state_time(c)[0] == 12
+    fb.lts_advance(c, 18)
+    h, u = fb.state_read(c)
+    assert np.array_equal(h, ref_h) and np.array_equal(u, ref_u)
+
+
+def test_run_host_matches_advance():
+    s = scenario.gaussian_bump_case(two_level=True)
+    a = make_state(s)
+    fb.lts_advance(a, 7)
+    ha, ua = fb.state_read(a)
+    b = make_state(s)
+    h = np.empty_like(s.h0)
+    u = np.empty_like(s.u0)
+    fb.run_host(b, np.ascontiguousarray(s.h0), np.ascontiguousarray(s.u0), 7, h, u)
+    assert np.array_equal(h, ha) and np.array_equal(u, ua)
+
+
+def test_write_read_roundtrip_caller_order():
+    s = scenario.shelf_case(nx=32, ny=16, dc=2e3, M=4, width=10e3)
+    st = make_state(s)
+    rng = np.random.default_rng(5)
+    h = s.h0 + rng.random(s.mesh.nCells)
+    u = rng.normal(size=s.mesh.nEdges)
+    u[s.mesh.boundary_edge_mask()] = 0.0
+    fb.state_write(st, h, u)
+    h2, u2 = fb.state_read(st)
+    assert np.array_equal(h, h2) and np.array_equal(u, u2)
+
+
+def test_instability_is_reported():
+    s = scenario.gaussian_bump_case(two_level=False)
+    st = make_state(s)
+    h = s.h0.copy()
+    h[10] = -5.0
+    fb.state_write(st, h, None)
+    fb.lts_advance(st, 1)
+    with pytest.raises(fb.FbltsError) as ei:
+        fb.synchronize(st)
+    assert ei.value.status == fb.E_UNSTABLE
+
+
+def test_bad_regions_rejected():
+    s = scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3))
+    bad = s.level.copy()
+    d = scenario.graph_distance(s.mesh, s.level == 2)
+    bad[(s.level == 1) & (d > 3)] = 0
+    with pytest.raises(fb.FbltsError) as ei:
+        fb.mesh_create(s.mesh, s.fVertex, level=bad, M=s.M)
+    assert ei.value.status == fb.E_REGIONS
