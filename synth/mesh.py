@@ -135,7 +135,8 @@ def build_from_triangles(pts, tri, period=None):
     flip = cross < 0
     tri[flip, 1], tri[flip, 2] = tri[flip, 2].copy(), tri[flip, 1].copy()
     db, dcv = np.where(flip[:, None], dcv, db), np.where(flip[:, None], db, dcv)
-    if np.any(np.abs(cross) < 1e-12 * (np.abs(db).max() ** 2 + 1e-300)):
+    scale = np.maximum((db ** 2).sum(1), (dcv ** 2).sum(1))
+    if np.any(np.abs(cross) <= 1e-13 * scale):
         raise ValueError("degenerate triangle")
 
     # circumcentres relative to vertex a

@@ -131,7 +131,7 @@ def test_instability_is_reported():
     s = scenario.gaussian_bump_case(two_level=False)
     st = make_state(s)
     h = s.h0.copy()
-    h[10] = -5.0
+    h[10] = np.nan          # a non-finite thickness planted on the host
     fb.state_write(st, h, None)
     fb.lts_advance(st, 1)
     with pytest.raises(fb.FbltsError) as ei:
