@@ -259,6 +259,34 @@ fblts_status fblts_state_profile_step(fblts_state *state, double *ms, int64_t *l
 fblts_status fblts_state_step_bytes(const fblts_state *state, double *alg_bytes,
                                     int64_t *cell_updates);
 
+/*
+ * Allocation-free global diagnostics.  The paper has no counterpart: this is
+ * a service for callers that must not allocate device memory during a run,
+ * for instance code that owns all device memory through its own pool, or a
+ * tight driver loop where cudaMalloc / cudaFree would synchronise the device
+ * and stall other work.
+ *
+ * Computes the same total mass and total absolute vorticity as
+ * fblts_diagnostics, from state arrays the caller already holds on the
+ * device: d_h[nCells] and d_u[nEdges] in the caller's cell / edge order.  The
+ * two results are written to the device array d_out[2] (mass, absolute
+ * vorticity) on `stream` (a cudaStream_t, NULL = legacy default stream);
+ * the call does not wait for them.
+ *
+ * The call allocates nothing.  Its scratch (one pair of partial sums per
+ * block of 8192 cells) is a static device array of 64 KiB, reserved on
+ * every GPU that loads the library until the process exits; it bounds the
+ * mesh to at most 33,554,432 cells and vertices (FBLTS_E_ARG beyond).  The
+ * first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the one array, and every call overwrites all the partial sums
+ * it reads (nothing carries over from an earlier call), so calls that
+ * overlap on the GPU race: order them on one stream or synchronise between
+ * them.  The mesh's device must be current.
+ */
+fblts_status fblts_diagnostics_static(const fblts_mesh *mesh, const double *d_h, const double *d_u,
+                                      double *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

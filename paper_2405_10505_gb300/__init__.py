@@ -64,7 +64,7 @@ SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts
            "fblts_state_init", "fblts_state_destroy", "fblts_lts_advance", "fblts_synchronize",
            "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
            "fblts_state_time", "fblts_state_save", "fblts_state_load", "fblts_state_launches_per_step",
-           "fblts_state_profile_step", "fblts_state_step_bytes")
+           "fblts_state_profile_step", "fblts_state_step_bytes", "fblts_diagnostics_static")
 PROFILE_KINDS = ("cell", "vertex", "edge_prep", "edge", "save", "predict", "correct", "forcing", "step_end")
 
 
@@ -100,6 +100,7 @@ def lib():
             "fblts_state_launches_per_step": [V, C.POINTER(C.c_int64)],
             "fblts_state_profile_step": [V, _PD, C.POINTER(C.c_int64), _PD],
             "fblts_state_step_bytes": [V, _PD, C.POINTER(C.c_int64)],
+            "fblts_diagnostics_static": [V, V, V, V, V],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -327,3 +328,13 @@ def state_step_bytes(state):
     b, cu = C.c_double(), C.c_int64()
     _check(lib().fblts_state_step_bytes(state.handle, C.byref(b), C.byref(cu)))
     return b.value, cu.value
+
+
+def diagnostics_static(mesh, d_h, d_u, d_out, stream=None):
+    """Allocation-free diagnostics on caller-order device arrays (raw device pointers).
+
+    Writes (mass, absolute vorticity) to the device array at ``d_out`` on
+    ``stream`` without waiting; see ``fblts_diagnostics_static``.
+    """
+    _check(lib().fblts_diagnostics_static(mesh.handle, C.c_void_p(d_h), C.c_void_p(d_u), C.c_void_p(d_out),
+                                          None if stream is None else C.c_void_p(stream)))

@@ -103,6 +103,16 @@ struct fblts_state {
 
 extern "C" const char *fblts_last_error(void) { return last_error_text(); }
 
+namespace fblts {
+// the mesh's device tables and permutations (used by the allocation-free diagnostics)
+const DevMesh *mesh_dev(const fblts_mesh *m, const int **cell_n2o, const int **edge_n2o, int *device) {
+    *cell_n2o = m->cell_n2o;
+    *edge_n2o = m->edge_n2o;
+    *device = m->device;
+    return &m->dm;
+}
+}  // namespace fblts
+
 // ------------------------------------------------------------------ mesh
 
 extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mesh **out) {
