@@ -56,24 +56,41 @@ def spacing(d, dx_min, dx_max, d0, slope):
 
 
 def _rows(coast, Ly, dx_min, dx_max, d0, slope, rng, jitter, margin):
+    """Coast-parallel rows of generators: ocean rows (d >= -4 dx_min) follow
+    dx(d); land rows east of them coarsen by 25 % per row up to dx_max until
+    the frame edge, so the cloud's hull is close to a rectangle."""
     ys = np.linspace(-margin, Ly + margin, 200001)
     xs = coast.x(ys)
     ds = np.sqrt(1.0 + np.gradient(xs, ys) ** 2)
     arc = np.concatenate([[0.0], np.cumsum(0.5 * (ds[1:] + ds[:-1]) * np.diff(ys))])
-    d = -4.0 * dx_min
-    dmax = coast.x(ys).max() + margin
-    pts = []
-    k = 0
-    while d <= dmax:
-        dx = float(spacing(np.array(d), dx_min, dx_max, d0, slope))
+
+    def row(d, dx, k):
         s = np.arange(0.0, arc[-1], dx) + (0.5 * dx if k % 2 else 0.0)
         y = np.interp(s, arc, ys)
         x = coast.x(y) - d
         if jitter:
             x = x + rng.uniform(-jitter, jitter, x.size) * dx
             y = y + rng.uniform(-jitter, jitter, y.size) * dx
-        pts.append(np.stack([x, y], 1))
+        return np.stack([x, y], 1)
+
+    pts = []
+    d = -4.0 * dx_min
+    dmax = coast.x(ys).max() + margin
+    k = 0
+    while d <= dmax:
+        dx = float(spacing(np.array(d), dx_min, dx_max, d0, slope))
+        pts.append(row(d, dx, k))
         d += np.sqrt(3.0) / 2.0 * dx
+        k += 1
+    # land rows
+    dx = dx_min
+    d = -4.0 * dx_min
+    dland = coast.x_off + coast.a.sum() + margin
+    k = 1
+    while d > -dland:
+        dx = min(dx_max, dx * 1.25)
+        d -= np.sqrt(3.0) / 2.0 * dx
+        pts.append(row(d, dx, k))
         k += 1
     return np.concatenate(pts)
 
@@ -103,7 +120,10 @@ def _lloyd(pts, coast, dx_min, dx_max, d0, slope, iters, movable):
                 cen = (p + u + v) / 3.0
                 dist = coast.x(cen[:, 1]) - cen[:, 0]
                 w = area * spacing(dist, dx_min, dx_max, d0, slope) ** -4
-                np.add.at(acc, tri[:, idx], np.stack([w * cen[:, 0], w * cen[:, 1], w], 1))
+                n = pts.shape[0]
+                acc[:, 0] += np.bincount(tri[:, idx], weights=w * cen[:, 0], minlength=n)
+                acc[:, 1] += np.bincount(tri[:, idx], weights=w * cen[:, 1], minlength=n)
+                acc[:, 2] += np.bincount(tri[:, idx], weights=w, minlength=n)
         good = (acc[:, 2] > 0) & movable
         pts = pts.copy()
         pts[good] = acc[good, :2] / acc[good, 2:3]
@@ -132,7 +152,11 @@ def basin_case(Ly=9600e3, Lx=1500e3, x_off=150e3, dx_min=500.0, dx_max=20e3, d0=
     if verbose:
         print(f"basin: voronoi {time.time() - t0:.1f}s")
     x, y = full.xCell, full.yCell
-    ocean = (x >= 0.0) & (y >= 0.0) & (y <= Ly) & (x <= coast.x(y))
+    ocean = (x >= 0.0) & (y >= 0.0) & (y <= Ly) & (x <= coast.x(y)) & ~full.open_cell
+    # drop ocean cells without an ocean neighbour (specks cut off by the coast)
+    nb = full.cellsOnCell
+    wet_nb = (np.where(nb >= 0, ocean[np.maximum(nb, 0)], False)).any(1)
+    ocean &= wet_nb
     mesh = finalize(apply_cell_mask(full, ocean))
     if verbose:
         print(f"basin: {mesh.nCells} cells {mesh.nEdges} edges {mesh.nVertices} vertices, {time.time() - t0:.1f}s")

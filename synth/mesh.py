@@ -225,32 +225,34 @@ def build_from_triangles(pts, tri, period=None):
     kiteOnCell[ii, kk] = kites[vv, jj]
 
     # edgesOnEdge / weightsOnEdge (see module docstring)
-    maxEdges2 = 2 * (maxEdges - 1)
+    slot_of = np.zeros((E, 2), np.int64)          # position of e in the lists of c0 / c1
+    slot_of[ee[isc0], 0] = slot[isc0]
+    slot_of[ee[~isc0], 1] = slot[~isc0]
+    closed = ~open_cell
+    ok = closed[c0] & closed[c1]
+    mclosed = int(nEdgesOnCell[closed].max()) if closed.any() else 3
+    maxEdges2 = 2 * (mclosed - 1)
     eoe = np.full((E, maxEdges2), -1, np.int64)
     woe = np.zeros((E, maxEdges2))
     neoe = np.zeros(E, np.int64)
-    closed = ~open_cell
-    ok = closed[c0] & closed[c1]
-    cols = 0
+    rows = np.arange(E)
     for side, csel, sgn_e in ((0, c0, 1.0), (1, c1, -1.0)):
         i = csel
-        n = nEdgesOnCell[i]
-        # position of e in cell i's list
-        p = np.argmax(edgesOnCell[i] == np.arange(E)[:, None], axis=1)
+        n = np.maximum(nEdgesOnCell[i], 1)
+        p = slot_of[:, side]
         rsum = np.zeros(E)
-        for m in range(1, maxEdges):
+        for m in range(1, mclosed):
             act = ok & (m < n)
-            prev = (p + m - 1) % np.maximum(n, 1)
+            prev = (p + m - 1) % n
             rsum = rsum + np.where(act, kiteOnCell[i, prev] / areaCell[i], 0.0)
-            idx = (p + m) % np.maximum(n, 1)
-            ej = edgesOnCell[i, idx]
-            sgn_j = np.where(c0[np.maximum(ej, 0)] == i, 1.0, -1.0)
-            w = sgn_e * sgn_j * (0.5 - rsum) * dvEdge[np.maximum(ej, 0)] / dcEdge
-            col = neoe.copy()
-            eoe[act, col[act]] = ej[act]
-            woe[act, col[act]] = w[act]
+            ej = edgesOnCell[i, (p + m) % n]
+            ejc = np.maximum(ej, 0)
+            sgn_j = np.where(c0[ejc] == i, 1.0, -1.0)
+            w = sgn_e * sgn_j * (0.5 - rsum) * dvEdge[ejc] / dcEdge
+            col = neoe[act]
+            eoe[rows[act], col] = ej[act]
+            woe[rows[act], col] = w[act]
             neoe = neoe + act
-        cols = max(cols, int(neoe.max()) if E else 0)
 
     return Mesh(
         cellsOnEdge=np.stack([c0, c1], 1), nEdgesOnCell=nEdgesOnCell, edgesOnCell=edgesOnCell,
@@ -294,12 +296,15 @@ def apply_cell_mask(mesh, keep):
     eoe[~interior] = -1
     woe[~interior] = 0.0
     neoe[~interior] = 0
+    mE = max(int(mesh.nEdgesOnCell[keep].max()), 3) if keep.any() else mesh.maxEdges
+    mE2 = max(int(neoe.max()), 1) if neoe.size else 1
+    eoe, woe = eoe[:, :mE2], woe[:, :mE2]
     out = Mesh(
         cellsOnEdge=new_coe,
         nEdgesOnCell=mesh.nEdgesOnCell[keep].copy(),
-        edgesOnCell=rm(emap, mesh.edgesOnCell[keep]),
-        verticesOnCell=rm(vmap, mesh.verticesOnCell[keep]),
-        cellsOnCell=rm(cmap, mesh.cellsOnCell[keep]),
+        edgesOnCell=rm(emap, mesh.edgesOnCell[keep][:, :mE]),
+        verticesOnCell=rm(vmap, mesh.verticesOnCell[keep][:, :mE]),
+        cellsOnCell=rm(cmap, mesh.cellsOnCell[keep][:, :mE]),
         verticesOnEdge=rm(vmap, mesh.verticesOnEdge[ekeep]),
         cellsOnVertex=rm(cmap, cov[vkeep]),
         edgesOnVertex=rm(emap, mesh.edgesOnVertex[vkeep]),
