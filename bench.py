@@ -39,6 +39,12 @@ def make_workload(name):
         s = scenario.shelf_case()
         desc = ("periodic-in-y 512x512 hex channel, dc 2 km, walls in x, tanh shelf 10-4000 m with 5% "
                 "roughness, 2 LTS levels (M=4) by gravity-wave CFL, 15 m/s wind stress + quadratic drag")
+    elif name == "basin":
+        from synth import basin
+        s = basin.basin_case()
+        desc = ("closed basin, variable-resolution Voronoi mesh (~2.0M cells): 500 m along a seeded sinuous "
+                "coast growing to 20 km offshore, depth 5-4000 m, 3 LTS levels (M=8) by gravity-wave CFL, "
+                "moving Holland vortex with wind stress, pressure gradient and quadratic drag")
     elif name == "bump":
         s = scenario.gaussian_bump_case(two_level=True)
         desc = "doubly periodic 32x32 hex, flat 1000 m, Gaussian bump, 2 LTS levels (M=2)"
@@ -192,8 +198,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fblts", choices=["fblts", "reference"])
-    ap.add_argument("--workload", default="shelf")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default="basin")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

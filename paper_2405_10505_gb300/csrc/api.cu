@@ -135,6 +135,7 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     std::vector<std::vector<int>> ikeep;
     std::vector<std::vector<double>> dkeep;
     std::vector<std::vector<unsigned char>> bkeep;
+    std::vector<std::vector<float>> fkeep;
     DevMesh &dm = m->dm;
     dm.nC = nC; dm.nE = nE; dm.nV = nV; dm.maxE = mE; dm.maxE2 = mE2;
     auto addi = [&](std::vector<int> v, const int **dst) {
@@ -145,7 +146,11 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
         dkeep.push_back(std::move(v));
         items.push_back({dkeep.back().data(), dkeep.back().size() * sizeof(double), (void **)dst});
     };
-    ikeep.reserve(32); dkeep.reserve(32); bkeep.reserve(2);
+    auto addf = [&](const std::vector<double> &v, const float **dst) {
+        fkeep.emplace_back(v.begin(), v.end());
+        items.push_back({fkeep.back().data(), fkeep.back().size() * sizeof(float), (void **)dst});
+    };
+    ikeep.reserve(32); dkeep.reserve(32); bkeep.reserve(2); fkeep.reserve(16);
     addi(hm.nEoC, &dm.nEoC);
     addi(slot_major(hm.eoc, nC, mE), &dm.eoc);
     addi(slot_major(hm.coc, nC, mE), &dm.coc);
@@ -169,6 +174,13 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     addd(slot_major(hm.cKite, nV, 3), &dm.cKite);
     addd(hm.fV, &dm.fV);
     addd(hm.Av, &dm.Av);
+    addf(slot_major(hm.cDiv, nC, mE), &dm.cDiv32);
+    addf(slot_major(hm.cKE, nC, mE), &dm.cKE32);
+    addf(slot_major(hm.woe, nE, mE2), &dm.woe32);
+    addf(hm.invDc, &dm.invDc32);
+    addf(slot_major(hm.cVort, nV, 3), &dm.cVort32);
+    addf(slot_major(hm.cKite, nV, 3), &dm.cKite32);
+    addf(hm.fV, &dm.fV32);
     addi(hm.cell_n2o, (const int **)&m->cell_n2o);
     addi(hm.cell_o2n, (const int **)&m->cell_o2n);
     addi(hm.edge_n2o, (const int **)&m->edge_n2o);
@@ -187,6 +199,12 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     std::vector<char> host(ar.size, 0);
     for (auto &it : items) {
         char *d = (char *)ar.take(it.bytes);
+        if (!d) {
+            set_error("mesh_create: arena layout error");
+            cudaFree(m->dbase);
+            delete m;
+            return FBLTS_E_OOM;
+        }
         std::memcpy(host.data() + (d - ar.base), it.src, it.bytes);
         *it.dst = d;
     }
@@ -278,6 +296,7 @@ static fblts_status upload_state(fblts_state *s, const double *h, const double *
         CK(launch_gather(s->arr.a[A_U], s->d_stage_e, m->edge_n2o, nE, s->st));
         CK(launch_zero_boundary(s->arr.a[A_U], s->dm.ebnd, nE, s->st));
     }
+    if (s->arr.fp32 && (h || u)) CK(launch_fp32_shadows(s->dm, s->arr, s->st));
     return FBLTS_OK;
 }
 
@@ -289,10 +308,6 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     if (!(p->dt > 0.0) || !(p->g > 0.0)) { set_error("state_init: dt and g must be positive"); return FBLTS_E_ARG; }
     if (p->precision != FBLTS_FP64 && p->precision != FBLTS_FP32_TENDENCY) {
         set_error("state_init: unknown precision %d", p->precision);
-        return FBLTS_E_ARG;
-    }
-    if (p->precision == FBLTS_FP32_TENDENCY) {
-        set_error("state_init: FBLTS_FP32_TENDENCY is not available in this build");
         return FBLTS_E_ARG;
     }
     if ((p->forcing & FBLTS_FORCE_WIND_STRESS) && !m->hm.has_angle) {
@@ -323,15 +338,30 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         }
         s->own_stream = true;
     }
-    // arena layout
+    // arena layout: FP64 path every array double; FP32 path the time level,
+    // correction sums and saved time level double, everything else float
+    const bool f32 = p->precision == FBLTS_FP32_TENDENCY;
+    auto is_double = [&](int a) {
+        return !f32 || a == A_H || a == A_U || a == A_ACCH || a == A_ACCU || a == A_SH0 || a == A_SU0;
+    };
+    auto count = [&](int a) -> size_t { return arr_is_cell(a) ? (size_t)nC : (arr_is_vert(a) ? (size_t)nV : (size_t)nE); };
+    // every allocation in order; the sizing pass and the carving pass walk the same list
+    size_t szc = sizeof(double) * (size_t)nC, sze = sizeof(double) * (size_t)nE;
+    std::vector<size_t> plan;
+    for (int a = 0; a < A_COUNT; ++a) plan.push_back(count(a) * (is_double(a) ? 8 : 4));
+    plan.push_back(szc);                                           // bottom
+    plan.push_back(sze); plan.push_back(sze); plan.push_back(sze); plan.push_back(szc);  // forcing (double)
+    if (f32) {
+        plan.push_back(4 * (size_t)nC); plan.push_back(4 * (size_t)nE);            // shadows
+        plan.push_back(4 * (size_t)nC); plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nV);  // depths
+        plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nE);
+        plan.push_back(4 * (size_t)nC);                                             // forcing (float)
+    }
+    plan.push_back(64);                                            // step counter + flag
+    plan.push_back(sizeof(double) * (2 * DIAG_BLOCKS + 2));        // diagnostics partials
+    plan.push_back(szc); plan.push_back(sze);                      // caller-order staging
     Arena ar;
-    size_t szc = sizeof(double) * (size_t)nC, sze = sizeof(double) * (size_t)nE, szv = sizeof(double) * (size_t)nV;
-    for (int a = 0; a < A_COUNT; ++a) ar.reserve(arr_is_cell(a) ? szc : (arr_is_vert(a) ? szv : sze));
-    ar.reserve(szc);                      // bottom
-    ar.reserve(sze * 3 + szc);            // forcing
-    ar.reserve(64);                       // step + flag
-    ar.reserve(sizeof(double) * (2 * DIAG_BLOCKS + 2));
-    ar.reserve(szc); ar.reserve(sze);     // staging
+    for (size_t b : plan) ar.reserve(b);
     ar.size = ar.used + 256;
     if (cudaMalloc(&s->dbase, ar.size) != cudaSuccess) {
         cudaGetLastError();
@@ -341,19 +371,46 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     }
     ar.base = (char *)s->dbase;
     ar.used = 0;
-    for (int a = 0; a < A_COUNT; ++a)
-        s->arr.a[a] = (double *)ar.take(arr_is_cell(a) ? szc : (arr_is_vert(a) ? szv : sze));
-    double *db = (double *)ar.take(szc);
-    s->fz.windN = (double *)ar.take(sze);
-    s->fz.windT = (double *)ar.take(sze);
-    s->fz.cw = (double *)ar.take(sze);
-    s->fz.ps = (double *)ar.take(szc);
-    s->d_step = (long long *)ar.take(64);
+    std::vector<void *> got;
+    for (size_t b : plan) {
+        void *ptr = ar.take(b);
+        if (!ptr) {
+            set_error("state_init: arena layout error");
+            fblts_state_destroy(s);
+            return FBLTS_E_OOM;
+        }
+        got.push_back(ptr);
+    }
+    size_t gi = 0;
+    s->arr.fp32 = f32 ? 1 : 0;
+    for (int a = 0; a < A_COUNT; ++a) {
+        void *ptr = got[gi++];
+        s->arr.a[a] = is_double(a) ? (double *)ptr : nullptr;
+        s->arr.f[a] = is_double(a) ? nullptr : (float *)ptr;
+    }
+    double *db = (double *)got[gi++];
+    s->fz.windN = (double *)got[gi++];
+    s->fz.windT = (double *)got[gi++];
+    s->fz.cw = (double *)got[gi++];
+    s->fz.ps = (double *)got[gi++];
+    float *H32 = nullptr, *He32 = nullptr, *Hv32 = nullptr;
+    if (f32) {
+        s->arr.xi32 = (float *)got[gi++];
+        s->arr.u32 = (float *)got[gi++];
+        H32 = (float *)got[gi++];
+        He32 = (float *)got[gi++];
+        Hv32 = (float *)got[gi++];
+        s->fz.windN32 = (float *)got[gi++];
+        s->fz.windT32 = (float *)got[gi++];
+        s->fz.cw32 = (float *)got[gi++];
+        s->fz.ps32 = (float *)got[gi++];
+    }
+    s->d_step = (long long *)got[gi++];
     s->d_flag = (int *)((char *)s->d_step + 16);
-    s->d_partials = (double *)ar.take(sizeof(double) * (2 * DIAG_BLOCKS + 2));
+    s->d_partials = (double *)got[gi++];
     s->d_diag = s->d_partials + 2 * DIAG_BLOCKS;
-    s->d_stage_c = (double *)ar.take(szc);
-    s->d_stage_e = (double *)ar.take(sze);
+    s->d_stage_c = (double *)got[gi++];
+    s->d_stage_e = (double *)got[gi++];
     if (cudaMemsetAsync(s->dbase, 0, ar.size, s->st) != cudaSuccess) {
         set_error("state_init: memset failed");
         fblts_state_destroy(s);
@@ -369,8 +426,17 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
             st = FBLTS_E_CUDA;
         }
     }
+    if (st == FBLTS_OK && f32) {
+        s->dm.H32 = H32; s->dm.He32 = He32; s->dm.Hv32 = Hv32;
+        if (launch_fp32_depths(s->dm, H32, He32, Hv32, s->st) != cudaSuccess ||
+            launch_fp32_shadows(s->dm, s->arr, s->st) != cudaSuccess) {
+            set_error("state_init: FP32 setup failed");
+            st = FBLTS_E_CUDA;
+        }
+    }
     if (st != FBLTS_OK) { fblts_state_destroy(s); return st; }
     DevForcing &fz = s->fz;
+    fz.fp32 = f32 ? 1 : 0;
     fz.flags = p->forcing;
     fz.wind_u = p->wind_u; fz.wind_v = p->wind_v; fz.cd = p->cd;
     fz.rho0 = p->rho0 > 0 ? p->rho0 : 1025.0;
@@ -378,7 +444,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     for (int k = 0; k < 9; ++k) fz.vx[k] = p->vortex[k];
     fz.t0 = p->t0; fz.dt = p->dt; fz.step = s->d_step;
     build_schedule(hm, p->dt, p->beta, s->sched);
-    schedule_bytes(hm, p->forcing, s->sched);
+    schedule_bytes(hm, p->forcing, p->precision == FBLTS_FP32_TENDENCY, s->sched);
     if (cudaStreamSynchronize(s->st) != cudaSuccess) {
         set_error("state_init: %s", cudaGetErrorString(cudaGetLastError()));
         fblts_state_destroy(s);

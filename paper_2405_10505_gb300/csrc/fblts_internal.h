@@ -127,6 +127,6 @@ struct Schedule {
 
 void build_schedule(const HostMesh &hm, double dt, const double beta[3], Schedule &s);
 // fills Op::alg_bytes of every op (forcing: the edge passes read the forcing fields)
-void schedule_bytes(const HostMesh &hm, int forcing_flags, Schedule &s);
+void schedule_bytes(const HostMesh &hm, int forcing_flags, bool fp32, Schedule &s);
 
 }  // namespace fblts

@@ -4,7 +4,7 @@
 // each index (stage update, in-place update, correction sum, kinetic energy
 // only) comes from the launch's segment list.  The passes use no atomics, so
 // every result is bit-reproducible run to run.
-#include "kernel_bodies.cuh"
+#include "kernel_bodies32.cuh"
 
 namespace fblts {
 
@@ -52,6 +52,68 @@ __global__ void __launch_bounds__(TPB) forcing_pass(DevMesh m, DevForcing fz) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const double time = fz.t0 + (double)(*fz.step) * fz.dt;
     forcing_body(m, fz, time, t);
+}
+
+__global__ void __launch_bounds__(TPB) cell32_pass(DevMesh m, CellArgs32 a) {
+    const int i = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.hi) cell32_body(m, a, i);
+}
+
+__global__ void __launch_bounds__(TPB) vert32_pass(DevMesh m, VertArgs32 a) {
+    const int v = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < a.hi) vert32_body(m, a, v);
+}
+
+__global__ void __launch_bounds__(TPB) eprep32_pass(DevMesh m, PrepArgs32 a) {
+    const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < a.hi) prep32_body(m, a, e);
+}
+
+template <bool FORCING>
+__global__ void __launch_bounds__(TPB) edge32_pass(DevMesh m, EdgeArgs32 a, DevForcing fz) {
+    const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < a.hi) edge32_body<FORCING>(m, a, fz, e);
+}
+
+__global__ void __launch_bounds__(TPB) save32_pass(IfArgs32 a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n) save32_body(a, t);
+}
+
+__global__ void __launch_bounds__(TPB) pred32_pass(IfArgs32 a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n) pred32_body(a, t);
+}
+
+__global__ void __launch_bounds__(TPB) final32_pass(IfArgs32 a, const unsigned char *ebnd) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n) final32_body(a, ebnd, t);
+}
+
+__global__ void __launch_bounds__(TPB) forcing32_pass(DevMesh m, DevForcing fz) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const double time = fz.t0 + (double)(*fz.step) * fz.dt;
+    forcing32_body(m, fz, time, t);
+}
+
+// resting depth seen by the FP32 path: H per cell, mean over the present cells
+// of an edge, kite-weighted mean at a vertex
+__global__ void fp32_depths(DevMesh m, float *H32, float *He32, float *Hv32) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m.nC) H32[t] = (float)(-m.bottom[t]);
+    if (t < m.nE) He32[t] = (float)(-0.5 * (m.bottom[m.coe0[t]] + m.bottom[m.coe1[t]]));
+    if (t < m.nV) {
+        double s = 0.0;
+        for (int j = 0; j < 3; ++j) s += m.cKite[j * m.nV + t] * (-m.bottom[m.cov[j * m.nV + t]]);
+        Hv32[t] = (float)s;
+    }
+}
+
+__global__ void fp32_shadows(const double *h, const double *b, const double *u, float *xi, float *u32, int nC,
+                             int nE) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nC) xi[t] = (float)(h[t] + b[t]);
+    if (t < nE) u32[t] = (float)u[t];
 }
 
 __global__ void step_end(long long *step) { *step += 1; }
@@ -129,8 +191,60 @@ inline int nblk(long long n) { return (int)((n + TPB - 1) / TPB); }
 
 }  // namespace
 
+static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &arr, const DevForcing &fz,
+                               double g, long long *step_counter, cudaStream_t st) {
+    switch (op.kind) {
+        case OP_CELL:
+            if (op.hi <= op.lo) return cudaSuccess;
+            cell32_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, cell_args32(op, arr, m));
+            break;
+        case OP_VERT:
+            if (op.hi <= op.lo) return cudaSuccess;
+            vert32_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, vert_args32(op, arr));
+            break;
+        case OP_EPREP:
+            if (op.hi <= op.lo) return cudaSuccess;
+            eprep32_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, prep_args32(op, arr));
+            break;
+        case OP_EDGE:
+            if (op.hi <= op.lo) return cudaSuccess;
+            if (fz.flags) edge32_pass<true><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, edge_args32(op, arr, g), fz);
+            else edge32_pass<false><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, edge_args32(op, arr, g), fz);
+            break;
+        case OP_SAVE:
+        case OP_PRED:
+        case OP_FINAL: {
+            IfArgs32 a = if_args32(op, arr, m);
+            if (a.n <= 0) return cudaSuccess;
+            if (op.kind == OP_SAVE) save32_pass<<<nblk(a.n), TPB, 0, st>>>(a);
+            else if (op.kind == OP_PRED) pred32_pass<<<nblk(a.n), TPB, 0, st>>>(a);
+            else final32_pass<<<nblk(a.n), TPB, 0, st>>>(a, m.ebnd);
+        } break;
+        case OP_FORCING:
+            if (!fz.flags) return cudaSuccess;
+            forcing32_pass<<<nblk(m.nE > m.nC ? m.nE : m.nC), TPB, 0, st>>>(m, fz);
+            break;
+        case OP_STEP_END: step_end<<<1, 1, 0, st>>>(step_counter); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp32_depths(const DevMesh &m, float *H32, float *He32, float *Hv32, cudaStream_t st) {
+    const int n = m.nE > m.nV ? (m.nE > m.nC ? m.nE : m.nC) : (m.nV > m.nC ? m.nV : m.nC);
+    fp32_depths<<<nblk(n), TPB, 0, st>>>(m, H32, He32, Hv32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp32_shadows(const DevMesh &m, const DevArrays &arr, cudaStream_t st) {
+    fp32_shadows<<<nblk(m.nE > m.nC ? m.nE : m.nC), TPB, 0, st>>>(arr.a[A_H], m.bottom, arr.a[A_U], arr.xi32,
+                                                                   arr.u32, m.nC, m.nE);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_op(const Op &op, const DevMesh &m, const DevArrays &arr, const DevForcing &fz, double g,
                       long long *step_counter, cudaStream_t st) {
+    if (arr.fp32) return launch_op32(op, m, arr, fz, g, step_counter, st);
     switch (op.kind) {
         case OP_CELL:
             if (op.hi <= op.lo) return cudaSuccess;

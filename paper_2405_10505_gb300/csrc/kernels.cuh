@@ -21,19 +21,34 @@ struct DevMesh {
     const double *cosE, *sinE, *xE, *yE, *xC, *yC;
     const int *eov, *cov;               // vertices
     const double *cVort, *cKite, *fV, *Av;
+    // single-precision copies of the coefficients (FP32-tendency path)
+    const float *cDiv32, *cKE32, *woe32, *invDc32, *cVort32, *cKite32, *fV32;
+    // resting depth H = -b as seen by the FP32 path: per cell, edge mean, vertex mean (per state)
+    const float *H32, *He32, *Hv32;
 };
 
 struct DevForcing {
     int flags;                 // FBLTS_FORCE_* bits
+    int fp32;                  // write the single-precision fields instead
     double *windN, *windT, *cw, *ps;
+    float *windN32, *windT32, *cw32, *ps32;   // ps32 = p_s - (pc + dp), the ambient-relative pressure
     double wind_u, wind_v, cd, rho0, rho_air;
     double vx[9];
     double t0, dt;
     const long long *step;     // device step counter
 };
 
+// State arrays by schedule id.  FP64 path: every array is double (a[]).
+// FP32-tendency path: the time level A_H / A_U, the correction sums A_ACCH /
+// A_ACCU and the saved time level A_SH0 / A_SU0 stay double (a[]); the stage
+// arrays, K, q, F, q_e and the saved IF-1 stage data are float (f[]), with
+// every thickness stored as xi = h - H (deviation from the resting depth);
+// xi32 / u32 are float shadows of the double time level.
 struct DevArrays {
     double *a[A_COUNT];
+    float *f[A_COUNT];
+    float *xi32, *u32;
+    int fp32;
 };
 
 struct SegSet {
@@ -44,6 +59,11 @@ struct SegSet {
 // launches one schedule op on the stream
 cudaError_t launch_op(const Op &op, const DevMesh &m, const DevArrays &arr, const DevForcing &fz,
                       double g, long long *step_counter, cudaStream_t st);
+
+// FP32-tendency path: resting depths seen by the float kernels, and the
+// float shadows of the double time level (after any write of h, u)
+cudaError_t launch_fp32_depths(const DevMesh &m, float *H32, float *He32, float *Hv32, cudaStream_t st);
+cudaError_t launch_fp32_shadows(const DevMesh &m, const DevArrays &arr, cudaStream_t st);
 
 // caller-order <-> band-order copies
 cudaError_t launch_gather(double *dst, const double *src, const int *idx, int n, cudaStream_t st);

@@ -235,14 +235,19 @@ private:
 }  // namespace
 
 // Algorithmic bytes of one launch: each array element its arithmetic reads or
-// writes, once, at storage size (int32 4, double 8, flag 1).  Gathered arrays
-// count one read per source element, using the incidence of the mesh: an edge
-// is shared by 2 cells and 2 vertices, a vertex by 3 cells and 3 edges.
-void schedule_bytes(const HostMesh &hm, int forcing, Schedule &s) {
+// writes, once, at storage size (int32 4, double 8, float 4, flag 1).
+// Gathered arrays count one read per source element, from the incidence of
+// the mesh: a pass over edges that gathers a cell array reads 2 nC/nE cell
+// elements per edge (2 cpe, cpe = nC/nE), a vertex array 2 nV/nE (2 vpe).
+// fp32: stage data, kinetic energy, PV, fluxes and coefficients in float; the
+// time level, the divergence coefficients and the correction sums in double.
+void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
     std::vector<double> pc(hm.nC + 1, 0.0), pe(hm.nE + 1, 0.0);
     for (int i = 0; i < hm.nC; ++i) pc[i + 1] = pc[i] + hm.nEoC[i];
     for (int e = 0; e < hm.nE; ++e) pe[e + 1] = pe[e] + hm.nEoE[e];
-    const double cpe = (double)hm.nC / hm.nE, vpe = (double)hm.nV / hm.nE;  // cells, vertices per edge
+    const double cpe = (double)hm.nC / hm.nE, vpe = (double)hm.nV / hm.nE;
+    const double R = fp32 ? 4.0 : 8.0;        // stage / scratch element
+    const double C = fp32 ? 4.0 : 8.0;        // coefficient element
     for (Op &op : s.ops) {
         double b = 0.0;
         switch (op.kind) {
@@ -250,33 +255,53 @@ void schedule_bytes(const HostMesh &hm, int forcing, Schedule &s) {
                 for (int k = 0; k < op.nseg; ++k) {
                     const Seg &g = op.seg[k];
                     const double n = g.end - g.begin, slots = pc[g.end] - pc[g.begin];
-                    if (g.mode == SEG_KONLY) { b += n * 12 + slots * (12 + 4); continue; }
-                    b += n * (4 + 8 + 8) + slots * (24 + 4);   // nEoC, h_in, K | eoc coc cDiv cKE, u_in
-                    if (g.mode == SEG_UPD || g.mode == SEG_INPLACE) b += n * (8 * 3 + (op.stage == 3 ? 8 : 0));
+                    // nEoC, K out | eoc, cKE, u_in (an edge is gathered by 2 cells)
+                    b += n * (4 + R) + slots * (4 + C + R / 2);
+                    if (g.mode == SEG_KONLY) continue;
+                    b += n * (R + (fp32 ? 4 : 0)) + slots * (4 + 8);   // h_in (+H) | coc, cDiv (double)
+                    if (g.mode == SEG_UPD) b += n * R * (3 + (op.stage == 3 ? 1 : 0));
+                    if (g.mode == SEG_INPLACE)
+                        b += n * (fp32 ? (8 + 8 + 8 + 4 + 4 + 4) : (8 + 8 + 8)) + n * (op.stage == 3 ? R : 0);
                     if (g.mode == SEG_ACC_SET) b += n * 8;
                     if (g.mode == SEG_ACC_ADD) b += n * 16;
                 }
                 break;
-            case OP_VERT: b = (double)(op.hi - op.lo) * (72 + 8 + 8 + 12 + 4); break;
-            case OP_EPREP: b = (double)(op.hi - op.lo) * (17 + 8 + 8 * 2 * cpe + 8 * 2 * vpe + 16); break;
+            case OP_VERT:
+                b = (double)(op.hi - op.lo) * (3 * (4 + 4 + C + C) + C + (fp32 ? 4 : 0) + 1.5 * R + 0.5 * R + R);
+                break;
+            case OP_EPREP:
+                b = (double)(op.hi - op.lo) * (17 + (fp32 ? 4 : 0) + R + R * 2 * cpe + R * 2 * vpe + 2 * R);
+                break;
             case OP_EDGE:
                 for (int k = 0; k < op.nseg; ++k) {
                     const Seg &g = op.seg[k];
                     const double n = g.end - g.begin, slots = pe[g.end] - pe[g.begin];
-                    b += n * (1 + 4 + 16 + 8 + 8 + 3 * 8 * 2 * cpe) + slots * 12;
-                    b += n * ((g.mode == SEG_UPD || g.mode == SEG_INPLACE || g.mode == SEG_ACC_ADD) ? 16 : 8);
-                    if (forcing) b += n * (8 + 24 + 8 * 2 * cpe);
+                    // ebnd, nEoE, Fe/qe, coe, invDc, K and hst at the cells (+ bottom in double)
+                    b += n * (1 + 4 + 2 * R + 8 + C + 2 * R * 2 * cpe + (fp32 ? 0 : 8 * 2 * cpe)) + slots * (4 + C);
+                    if (g.mode == SEG_UPD) b += n * 2 * R;
+                    if (g.mode == SEG_INPLACE) b += n * (fp32 ? (8 + 8 + 4) : 16);
+                    if (g.mode == SEG_ACC_SET) b += n * 8;
+                    if (g.mode == SEG_ACC_ADD) b += n * 16;
+                    if (forcing) b += n * (R + 3 * R + (fp32 ? 4 : 0) + R * 2 * cpe);
                 }
                 break;
-            case OP_SAVE:
-                b = 64.0 * (op.c_if1_hi - op.c_if1_lo) + 16.0 * (op.c_if12_hi - op.c_if1_hi) +
-                    64.0 * (op.e_if1_hi - op.e_if1_lo) + 16.0 * (op.e_if12_hi - op.e_if1_hi);
+            case OP_SAVE: {
+                const double big = fp32 ? (16 + 3 * 8) : 64;   // h^n copy + 3 stage copies
+                b = big * (op.c_if1_hi - op.c_if1_lo) + 16.0 * (op.c_if12_hi - op.c_if1_hi) +
+                    big * (op.e_if1_hi - op.e_if1_lo) + 16.0 * (op.e_if12_hi - op.e_if1_hi);
+            } break;
+            case OP_PRED:
+                b = (fp32 ? 52.0 : 80.0) * (op.c_if1_hi - op.c_if1_lo) +
+                    (fp32 ? 32.0 : 56.0) * (op.e_if1_hi - op.e_if1_lo);
                 break;
-            case OP_PRED: b = 80.0 * (op.c_if1_hi - op.c_if1_lo) + 56.0 * (op.e_if1_hi - op.e_if1_lo); break;
-            case OP_FINAL: b = 24.0 * (op.c_if12_hi - op.c_if1_lo) + 25.0 * (op.e_if12_hi - op.e_if1_lo); break;
+            case OP_FINAL:
+                b = (fp32 ? 36.0 : 24.0) * (op.c_if12_hi - op.c_if1_lo) +
+                    (fp32 ? 29.0 : 25.0) * (op.e_if12_hi - op.e_if1_lo);
+                break;
             case OP_FORCING:
-                if (forcing) b = (double)hm.nE * (16 + 24 + ((forcing & FBLTS_FORCE_VORTEX) ? 16 : 0)) +
-                                 (double)hm.nC * (8 + ((forcing & FBLTS_FORCE_VORTEX) ? 16 : 0));
+                if (forcing)
+                    b = (double)hm.nE * (16 + 3 * R + ((forcing & FBLTS_FORCE_VORTEX) ? 16 : 0)) +
+                        (double)hm.nC * (R + ((forcing & FBLTS_FORCE_VORTEX) ? 16 : 0));
                 break;
             case OP_STEP_END: b = 16; break;
             default: break;

@@ -147,3 +147,17 @@ def test_bad_regions_rejected():
     with pytest.raises(fb.FbltsError) as ei:
         fb.mesh_create(s.mesh, s.fVertex, level=bad, M=s.M)
     assert ei.value.status == fb.E_REGIONS
+
+
+@pytest.mark.parametrize("precision", [fb.FP64, fb.FP32_TENDENCY])
+def test_odd_sized_arrays(precision):
+    """Array sizes that are not multiples of the arena alignment (37 x 22 cells)."""
+    s = scenario.shelf_case(nx=37, ny=22, dc=2e3, M=4, width=10e3)
+    assert (s.mesh.nCells * 8) % 256 and (s.mesh.nEdges * 8) % 256
+    st = make_state(s, precision=precision)
+    fb.lts_advance(st, 20)
+    h, u = fb.state_read(st)
+    ho, uo = _oracle(s, 20)
+    dh, du = rel_errors(h, u, ho, uo)
+    tol = TOL if precision == fb.FP64 else 1e-5
+    assert dh <= tol and du <= tol, (dh, du)
