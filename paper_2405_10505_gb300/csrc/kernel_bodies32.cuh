@@ -281,26 +281,45 @@ FB_HD void final32_body(const IfArgs32 &a, const unsigned char *ebnd, int t) {
     }
 }
 
+// Moving Holland-type vortex in float (the FP32 path): the offset from the
+// centre is formed in double, the profile p = pc + dp exp(-(R/r)^B) and the
+// gradient wind V = sqrt(B dp/rho_air (R/r)^B exp(-(R/r)^B) + (r f/2)^2) - r f/2
+// in float; returns p - (pc + dp), the pressure relative to ambient.
+FB_HD float vortex_at32(const DevForcing &fz, double x, double y, double t, float &wu, float &wv) {
+    const float rx = (float)(x - (fz.vx[4] + fz.vx[6] * t)), ry = (float)(y - (fz.vx[5] + fz.vx[7] * t));
+    const float r = sqrtf(rx * rx + ry * ry);
+    wu = 0.f;
+    wv = 0.f;
+    if (!(r > 0.f)) return -(float)fz.vx[1];
+    const float A = powf((float)fz.vx[2] / r, (float)fz.vx[3]);
+    const float ex = expf(-A);
+    if (ex == 0.f) return -(float)fz.vx[1];
+    const float hf = 0.5f * r * (float)fz.vx[8];
+    const float V = sqrtf((float)fz.vx[3] * (float)fz.vx[1] / (float)fz.rho_air * A * ex + hf * hf) - hf;
+    wu = -V * ry / r;
+    wv = V * rx / r;
+    return (float)fz.vx[1] * (ex - 1.f);
+}
+
 // Float copies of the forcing fields: ps32 relative to the ambient pc + dp.
 FB_HD void forcing32_body(const DevMesh &m, const DevForcing &fz, double time, int t) {
     if (t < m.nE) {
-        double wu = fz.wind_u, wv = fz.wind_v;
+        float wu = (float)fz.wind_u, wv = (float)fz.wind_v;
         if (fz.flags & FBLTS_FORCE_VORTEX) {
-            double p, a, b;
-            vortex_at(fz, m.xE[t], m.yE[t], time, p, a, b);
+            float a, b;
+            vortex_at32(fz, m.xE[t], m.yE[t], time, a, b);
             wu += a;
             wv += b;
         }
-        const double c = m.cosE[t], s = m.sinE[t];
-        const double wn = wu * c + wv * s, wt = -wu * s + wv * c;
-        fz.windN32[t] = (float)wn;
-        fz.windT32[t] = (float)wt;
-        fz.cw32[t] = (float)((fz.rho_air / fz.rho0) * (0.75 + 0.067 * sqrt(wn * wn + wt * wt)) * 1e-3);
+        const float c = (float)m.cosE[t], s = (float)m.sinE[t];
+        const float wn = wu * c + wv * s, wt = -wu * s + wv * c;
+        fz.windN32[t] = wn;
+        fz.windT32[t] = wt;
+        fz.cw32[t] = (float)(fz.rho_air / fz.rho0) * (0.75f + 0.067f * sqrtf(wn * wn + wt * wt)) * 1e-3f;
     }
     if (t < m.nC) {
-        double p = fz.vx[0] + fz.vx[1], a, b;
-        if (fz.flags & FBLTS_FORCE_VORTEX) vortex_at(fz, m.xC[t], m.yC[t], time, p, a, b);
-        fz.ps32[t] = (float)(p - (fz.vx[0] + fz.vx[1]));
+        float a, b;
+        fz.ps32[t] = (fz.flags & FBLTS_FORCE_VORTEX) ? vortex_at32(fz, m.xC[t], m.yC[t], time, a, b) : 0.f;
     }
 }
 

@@ -131,7 +131,8 @@ def _lloyd(pts, coast, dx_min, dx_max, d0, slope, iters, movable):
 
 
 def basin_case(Ly=9600e3, Lx=1500e3, x_off=150e3, dx_min=500.0, dx_max=20e3, d0=20e3, slope=0.02,
-               M=8, nlevels=3, lloyd=2, jitter=0.05, f=1e-4, seed=2405, verbose=False):
+               M=8, nlevels=3, lloyd=2, jitter=0.05, f=1e-4, seed=2405, vortex_offshore=600e3,
+               dt0_fit=False, verbose=False):
     """The ~2M-cell closed basin (defaults); smaller Ly gives a proportionally smaller mesh."""
     rng = _rng(seed)
     t0 = time.time()
@@ -172,14 +173,16 @@ def basin_case(Ly=9600e3, Lx=1500e3, x_off=150e3, dx_min=500.0, dx_max=20e3, d0=
     nominal = spacing(d, dx_min, dx_max, d0, slope)
     coarse = nominal >= 0.99 * dx_max
     dt0 = 0.95 * float(lim[coarse].min() if coarse.any() else lim.max())
+    if dt0_fit:   # small test basins: the finest level takes the smallest limit
+        dt0 = min(dt0, 0.95 * float(lim.min()) * float(M) ** (nlevels - 1))
     lev = np.ceil(np.log(dt0 / lim) / np.log(M) - 1e-12)
     lev = np.clip(lev, 0, nlevels - 1).astype(np.int32)
     if np.any(dt0 / float(M) ** lev > lim * (1 + 1e-12)):
         raise RuntimeError("basin: finest level too coarse for the CFL limit; add levels")
     lev = enforce_level_separation(mesh, lev).astype(np.int32)
-    # Holland vortex: starts 600 km offshore at a seeded latitude, moves east at 5 m/s
+    # Holland vortex: starts vortex_offshore (600 km) offshore at a seeded latitude, moves east at 5 m/s
     y0 = rng.uniform(0.35, 0.65) * Ly
-    x0 = float(coast.x(np.array([y0]))[0]) - 600e3
+    x0 = float(coast.x(np.array([y0]))[0]) - vortex_offshore
     vortex = (95000.0, 5000.0, float(rng.uniform(30e3, 60e3)), float(rng.uniform(1.2, 1.8)),
               x0, y0, 5.0, float(rng.uniform(-1.0, 1.0)))
     fz = Forcing(wind_u=0.0, wind_v=0.0, cd=2.5e-3, wind_stress=True, vortex=vortex)

@@ -157,7 +157,7 @@ def gaussian_bump_case(nx=32, ny=32, dc=10e3, H=1000.0, f=1e-4, amp=1.0, efold=1
 
 
 def shelf_case(nx=512, ny=512, dc=2e3, f=1e-4, seed=2405, M=4, wind=15.0, cd=2.5e-3,
-               roughness=0.05, width=20e3, fine_frac_cfl=0.5):
+               roughness=0.05, width=20e3, fine_frac_cfl=0.5, vortex=False):
     """Periodic-in-y hex channel with walls in x and a continental shelf.
 
     ``H(x) = 10 + 3990 (1 + tanh((x - x0)/width)) / 2`` with ``x0`` the
@@ -183,7 +183,12 @@ def shelf_case(nx=512, ny=512, dc=2e3, f=1e-4, seed=2405, M=4, wind=15.0, cd=2.5
     level = fine.astype(np.int32)
     h0 = H.copy()
     u0 = np.zeros(mesh.nEdges)
-    fz = Forcing(wind_u=-wind, wind_v=0.0, cd=cd, wind_stress=wind != 0.0)
+    vt = None
+    if vortex:   # a Holland vortex crossing the channel (plain distances, no periodic image)
+        Ly = ny * dc * SQRT3 / 2
+        vt = (95000.0, 5000.0, float(rng.uniform(8.0, 12.0)) * dc, float(rng.uniform(1.2, 1.8)),
+              0.3 * Lx, 0.5 * Ly, 5.0, 1.0)
+    fz = Forcing(wind_u=-wind, wind_v=0.0, cd=cd, wind_stress=wind != 0.0, vortex=vt)
     return Scenario(name=f"shelf_hex{nx}x{ny}", mesh=mesh, bottom=-H,
                     fVertex=np.full(mesh.nVertices, f), h0=h0, u0=u0, level=level,
                     M=[M], dt=float(dt_c), forcing=fz)

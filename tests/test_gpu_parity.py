@@ -30,6 +30,7 @@ CASES = {
     "bump_lts_m5": (lambda: scenario.gaussian_bump_case(two_level=True), 30, [5]),
     "shelf_forced_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3), 100, None),
     "nested_3level": (lambda: scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3)), 40, None),
+    "shelf_vortex_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3, vortex=True), 60, None),
 }
 
 
