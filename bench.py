@@ -48,7 +48,7 @@ def make_workload(name):
     elif name == "basin_small":
         from synth import basin
         s = basin.basin_case(Ly=1200e3)
-        desc = "1/8-length sample of the basin workload (same recipe, Ly 1200 km, ~0.44M cells)"
+        desc = "1/8-length sample of the basin workload (same recipe, Ly 1200 km, ~0.25M cells)"
     elif name == "bump":
         s = scenario.gaussian_bump_case(two_level=True)
         desc = "doubly periodic 32x32 hex, flat 1000 m, Gaussian bump, 2 LTS levels (M=2)"

@@ -139,8 +139,12 @@ typedef struct fblts_mesh_info {
     int64_t cells_per_level[8];
     /* cell-updates per coarse step: sum_l N_l * prod_{m<l} M_m */
     int64_t cell_updates_per_step;
-    /* fine-level cell updates of FB-LTS done on IF-1/IF-2 and F^l bands */
+    /* IF-1 u IF-2 cells of each level pair */
     int64_t band_cells[8];
+    /* bit 0: the FP32 edge pass reads neighbour edges from the two cells'
+     * edge rows (every edgesOnEdge list is the other edges of the edge's two
+     * cells); otherwise it reads the edgesOnEdge lists */
+    int32_t flags;
 } fblts_mesh_info;
 fblts_status fblts_mesh_get_info(const fblts_mesh *mesh, fblts_mesh_info *info);
 

@@ -42,7 +42,7 @@ class MeshDesc(C.Structure):
 class MeshInfo(C.Structure):
     _fields_ = [("nCells", C.c_int32), ("nEdges", C.c_int32), ("nVertices", C.c_int32),
                 ("nLevels", C.c_int32), ("cells_per_level", C.c_int64 * 8),
-                ("cell_updates_per_step", C.c_int64), ("band_cells", C.c_int64 * 8)]
+                ("cell_updates_per_step", C.c_int64), ("band_cells", C.c_int64 * 8), ("flags", C.c_int32)]
 
 
 class Params(C.Structure):

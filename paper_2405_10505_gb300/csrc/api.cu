@@ -150,7 +150,7 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
         fkeep.emplace_back(v.begin(), v.end());
         items.push_back({fkeep.back().data(), fkeep.back().size() * sizeof(float), (void **)dst});
     };
-    ikeep.reserve(32); dkeep.reserve(32); bkeep.reserve(2); fkeep.reserve(16);
+    ikeep.reserve(32); dkeep.reserve(32); bkeep.reserve(4); fkeep.reserve(16);
     addi(hm.nEoC, &dm.nEoC);
     addi(slot_major(hm.eoc, nC, mE), &dm.eoc);
     addi(slot_major(hm.coc, nC, mE), &dm.coc);
@@ -181,6 +181,18 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     addf(slot_major(hm.cVort, nV, 3), &dm.cVort32);
     addf(slot_major(hm.cKite, nV, 3), &dm.cKite32);
     addf(hm.fV, &dm.fV32);
+    addi(slot_major(hm.eocS, nC, mE), &dm.eocS);
+    addf(hm.dvE, &dm.dv32);
+    addf(hm.keE, &dm.ke32);
+    addd(hm.invA, &dm.invA);
+    dm.rows = hm.rows_canonical ? 1 : 0;
+    if (dm.rows) {
+        addf(slot_major(hm.woeC, nE, mE2), &dm.woeC32);
+        std::vector<unsigned char> sl(hm.eslot.size() * 2);
+        std::memcpy(sl.data(), hm.eslot.data(), sl.size());
+        bkeep.push_back(std::move(sl));
+        items.push_back({bkeep.back().data(), bkeep.back().size(), (void **)&dm.eslot});
+    }
     addi(hm.cell_n2o, (const int **)&m->cell_n2o);
     addi(hm.cell_o2n, (const int **)&m->cell_o2n);
     addi(hm.edge_n2o, (const int **)&m->edge_n2o);
@@ -233,6 +245,7 @@ extern "C" fblts_status fblts_mesh_get_info(const fblts_mesh *m, fblts_mesh_info
     info->nCells = hm.nC; info->nEdges = hm.nE; info->nVertices = hm.nV; info->nLevels = hm.L;
     for (int l = 0; l < hm.L && l < 8; ++l) info->cells_per_level[l] = hm.cells_per_level[l];
     info->cell_updates_per_step = hm.cell_updates_per_step;
+    info->flags = hm.rows_canonical ? 1 : 0;
     // band sizes: IF-1 u IF-2 cells of each level pair
     for (int l = 0; l + 1 < hm.L && l < 8; ++l) {
         uint32_t k0 = BandKey::make(hm.L, l, 0, 0);

@@ -43,6 +43,8 @@ struct HostMesh {
 
     // connectivity in new order (row-major per element; SoA on the device)
     std::vector<int> nEoC, eoc, coc;       // [nC], [nC*maxE], [nC*maxE]
+    std::vector<int> eocS;                 // eoc with the sign n_{e,i}: e (first cell) or ~e (second)
+    std::vector<double> dvE, keE, invA;    // l_e, d_e l_e / 4 per edge (0 on no-flow edges); 1/A_i
     std::vector<int> coe, voe;             // [nE*2]
     std::vector<int> cov, eov;             // [nV*3]
     std::vector<int> nEoE, eoe;            // [nE], [nE*maxE2]
@@ -51,6 +53,12 @@ struct HostMesh {
     std::vector<double> cDiv, cKE;         // [nC*maxE]
     std::vector<double> cVort, cKite;      // [nV*3]
     std::vector<double> woe;               // [nE*maxE2]
+    // Neighbour edges read from the two cells' edge rows: slot of the edge in
+    // the row of c0 (low byte) and c1 (high byte), and the weights reordered to
+    // [row of c0 from slot+1 cyclically, row of c1 from slot+1 cyclically].
+    bool rows_canonical = false;
+    std::vector<uint16_t> eslot;           // [nE]
+    std::vector<double> woeC;              // [nE*maxE2]
     std::vector<double> invDc, area, fV, Av;
     std::vector<double> cosE, sinE, xC, yC, xE, yE;
     bool has_angle = false, has_xy_cell = false, has_xy_edge = false;

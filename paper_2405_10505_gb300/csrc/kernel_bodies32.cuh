@@ -108,32 +108,37 @@ inline IfArgs32 if_args32(const Op &op, const DevArrays &arr, const DevMesh &m) 
 
 // Cell i, FP32 tendency: the edge flux F_e = (H_e + (xi_i + xi_nb)/2) u_e in
 // float (bit-identical from both cells of the edge: the sums commute), the
-// divergence Psi_i = sum_j cDiv_ij F_e accumulated in double with the double
-// coefficients, so the fluxes of an edge cancel in sum_i A_i h_i to double
-// roundoff (Eq. trisk_thickness, Theorem 1); the stage value
-// xi_s = xi0 + c tau Psi, in place h += c tau Psi in double (Eq. fbrk32), and
-// the FB average in xi.
+// divergence Psi_i = -(1/A_i) sum_j n_{e,i} l_e F_e accumulated in double
+// from the float products l_e F_e (exact in double and the same from both
+// cells), so the fluxes of an edge cancel in sum_i A_i h_i to double roundoff
+// (Eq. trisk_thickness, Theorem 1); K_i = (1/A_i) sum_j (d_e l_e / 4) u_e^2;
+// the stage value xi_s = xi0 + c tau Psi, in place h += c tau Psi in double
+// (Eq. fbrk32), and the FB average in xi.
 FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     const int mode = seg_mode(a.segs, i);
     if (mode == SEG_NONE) return;
     const int n = m.nEoC[i];
     const int nC = m.nC;
-    double psi = 0.0;
+    double S = 0.0;
     float ke = 0.f;
     const float xi_i = a.xi_in[i];
     const float H_i = m.H32[i];
     for (int j = 0; j < n; ++j) {
-        const int e = m.eoc[j * nC + i];
+        const int v = m.eocS[j * nC + i];
+        const int e = v < 0 ? ~v : v;
         const float ue = a.u_in[e];
-        ke += m.cKE32[j * nC + i] * ue * ue;
+        ke += m.ke32[e] * ue * ue;
         if (mode != SEG_KONLY) {
             const int nb = m.coc[j * nC + i];
             const float he = 0.5f * (H_i + m.H32[nb]) + 0.5f * (xi_i + a.xi_in[nb]);
             const float F = he * ue;
-            psi += m.cDiv[j * nC + i] * (double)F;
+            // n_{e,i} = +1 for the first cell: its outflow lowers h
+            S = fma(v < 0 ? (double)m.dv32[e] : -(double)m.dv32[e], (double)F, S);
         }
     }
-    a.K[i] = ke;
+    const double invA = m.invA[i];
+    a.K[i] = ke * (float)invA;
+    const double psi = S * invA;
     switch (mode) {
         case SEG_UPD: {
             const float x0 = a.xi0[i];
@@ -188,11 +193,33 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
         const int n = m.nEoE[e];
         const float qself = a.qe[e];
         float cor = 0.f, vt = 0.f;
-        for (int j = 0; j < n; ++j) {
-            const int x = m.eoe[j * nE + e];
-            const float w = m.woe32[j * nE + e];
-            cor += w * a.Fe[x] * (0.5f * (qself + a.qe[x]));
-            if (FORCING) vt += w * a.u_in[x];
+        if (m.rows) {
+            // neighbours = the other edges of c0 then of c1, from the cells' rows
+            const int nC = m.nC;
+            const unsigned short sl = m.eslot[e];
+            int k = 0;
+            for (int side = 0; side < 2; ++side) {
+                const int c = side ? c1 : c0;
+                const int nc = m.nEoC[c];
+                const int p = side ? (sl >> 8) : (sl & 0xff);
+                for (int j = 1; j < nc; ++j) {
+                    int jj = p + j;
+                    if (jj >= nc) jj -= nc;
+                    const int xs = m.eocS[jj * nC + c];
+                    const int x = xs < 0 ? ~xs : xs;
+                    const float w = m.woeC32[k * nE + e];
+                    ++k;
+                    cor += w * a.Fe[x] * (0.5f * (qself + a.qe[x]));
+                    if (FORCING) vt += w * a.u_in[x];
+                }
+            }
+        } else {
+            for (int j = 0; j < n; ++j) {
+                const int x = m.eoe[j * nE + e];
+                const float w = m.woe32[j * nE + e];
+                cor += w * a.Fe[x] * (0.5f * (qself + a.qe[x]));
+                if (FORCING) vt += w * a.u_in[x];
+            }
         }
         const float x0c = a.hst[c0], x1c = a.hst[c1];
         const float grad = (a.K[c1] - a.K[c0]) + a.g * (x1c - x0c);

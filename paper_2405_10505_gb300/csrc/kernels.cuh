@@ -23,6 +23,13 @@ struct DevMesh {
     const double *cVort, *cKite, *fV, *Av;
     // single-precision copies of the coefficients (FP32-tendency path)
     const float *cDiv32, *cKE32, *woe32, *invDc32, *cVort32, *cKite32, *fV32;
+    // neighbour edges from the cells' edge rows: slots and weights in row order (FP32 path)
+    const int *eocS;                    // edge rows with the sign n_{e,i} (~e for the second cell)
+    const float *dv32, *ke32;           // l_e and d_e l_e / 4 per edge
+    const double *invA;                 // 1 / A_i
+    int rows;                           // 1 when eslot / woeC32 are valid
+    const unsigned short *eslot;
+    const float *woeC32;
     // resting depth H = -b as seen by the FP32 path: per cell, edge mean, vertex mean (per state)
     const float *H32, *He32, *Hv32;
 };

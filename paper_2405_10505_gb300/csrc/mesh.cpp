@@ -449,6 +449,51 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
             }
         }
     }
+    // signed edge rows and per-edge metrics of the FP32 cell pass
+    hm.eocS.assign((size_t)nC * mE, 0);
+    hm.invA.resize(nC);
+    for (int i = 0; i < nC; ++i) {
+        hm.invA[i] = 1.0 / hm.area[i];
+        for (int j = 0; j < mE; ++j) {
+            const int e = hm.eoc[(size_t)i * mE + j];
+            hm.eocS[(size_t)i * mE + j] = (j < hm.nEoC[i] && !hm.ebnd[e] && hm.coe[2 * e + 1] == i) ? ~e : e;
+        }
+    }
+    hm.dvE.assign(nE, 0.0);
+    hm.keE.assign(nE, 0.0);
+    for (int e = 0; e < nE; ++e) {
+        const int eo = hm.edge_n2o[e];
+        if (hm.ebnd[e]) continue;
+        hm.dvE[e] = d->dvEdge[eo];
+        hm.keE[e] = 0.25 * d->dcEdge[eo] * d->dvEdge[eo];
+    }
+    // neighbour edges as the two cells' edge rows (see HostMesh::rows_canonical)
+    hm.eslot.assign(nE, 0);
+    hm.woeC.assign((size_t)nE * mE2, 0.0);
+    hm.rows_canonical = mE <= 255 && 2 * (mE - 1) <= mE2;
+    for (int e = 0; e < nE && hm.rows_canonical; ++e) {
+        if (hm.ebnd[e]) continue;
+        int k = 0, matched = 0;
+        int slot[2] = {0, 0};
+        for (int side = 0; side < 2; ++side) {
+            const int c = hm.coe[2 * e + side];
+            const int n = hm.nEoC[c];
+            int p = -1;
+            for (int j = 0; j < n; ++j) if (hm.eoc[(size_t)c * mE + j] == e) p = j;
+            if (p < 0) { hm.rows_canonical = false; break; }
+            slot[side] = p;
+            for (int j = 1; j < n; ++j) {
+                const int x = hm.eoc[(size_t)c * mE + (p + j) % n];
+                double w = 0.0;
+                for (int q = 0; q < hm.nEoE[e]; ++q)
+                    if (hm.eoe[(size_t)e * mE2 + q] == x) { w = hm.woe[(size_t)e * mE2 + q]; ++matched; }
+                hm.woeC[(size_t)e * mE2 + k++] = w;
+            }
+        }
+        if (!hm.rows_canonical) break;
+        if (matched != hm.nEoE[e]) hm.rows_canonical = false;   // a neighbour outside the two cells
+        hm.eslot[e] = (uint16_t)(slot[0] | (slot[1] << 8));
+    }
     hm.cells_per_level = per_level;
     int64_t cu = 0, mult = 1;
     for (int l = 0; l < L; ++l) {

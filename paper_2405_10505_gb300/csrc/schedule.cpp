@@ -255,10 +255,17 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
                 for (int k = 0; k < op.nseg; ++k) {
                     const Seg &g = op.seg[k];
                     const double n = g.end - g.begin, slots = pc[g.end] - pc[g.begin];
-                    // nEoC, K out | eoc, cKE, u_in (an edge is gathered by 2 cells)
-                    b += n * (4 + R) + slots * (4 + C + R / 2);
-                    if (g.mode == SEG_KONLY) continue;
-                    b += n * (R + (fp32 ? 4 : 0)) + slots * (4 + 8);   // h_in (+H) | coc, cDiv (double)
+                    if (fp32) {
+                        // nEoC, 1/A, K | signed edge row, u_in and l_e, d_e l_e/4 (an edge has 2 cells)
+                        b += n * (4 + 8 + 4) + slots * (4 + 2 + 2);
+                        if (g.mode == SEG_KONLY) continue;
+                        b += n * (4 + 4) + slots * (4 + 2);          // xi_in, H | coc, l_e
+                    } else {
+                        // nEoC, K out | eoc, cKE, u_in (an edge is gathered by 2 cells)
+                        b += n * (4 + 8) + slots * (4 + 8 + 4);
+                        if (g.mode == SEG_KONLY) continue;
+                        b += n * 8 + slots * (4 + 8);                // h_in | coc, cDiv
+                    }
                     if (g.mode == SEG_UPD) b += n * R * (3 + (op.stage == 3 ? 1 : 0));
                     if (g.mode == SEG_INPLACE)
                         b += n * (fp32 ? (8 + 8 + 8 + 4 + 4 + 4) : (8 + 8 + 8)) + n * (op.stage == 3 ? R : 0);
@@ -276,8 +283,14 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
                 for (int k = 0; k < op.nseg; ++k) {
                     const Seg &g = op.seg[k];
                     const double n = g.end - g.begin, slots = pe[g.end] - pe[g.begin];
-                    // ebnd, nEoE, Fe/qe, coe, invDc, K and hst at the cells (+ bottom in double)
-                    b += n * (1 + 4 + 2 * R + 8 + C + 2 * R * 2 * cpe + (fp32 ? 0 : 8 * 2 * cpe)) + slots * (4 + C);
+                    // ebnd, nEoE, Fe/qe, coe, invDc, K and hst at the cells (+ bottom in double);
+                    // neighbours: an index and a weight per slot, or (rows) the two cells' edge
+                    // rows, each row shared by the cell's edges, plus the two slots
+                    b += n * (1 + 4 + 2 * R + 8 + C + 2 * R * 2 * cpe + (fp32 ? 0 : 8 * 2 * cpe));
+                    if (fp32 && hm.rows_canonical)
+                        b += n * (2 + 2 * cpe * (4 + 4 * (pc[hm.nC] / hm.nC))) + slots * C;
+                    else
+                        b += slots * (4 + C);
                     if (g.mode == SEG_UPD) b += n * 2 * R;
                     if (g.mode == SEG_INPLACE) b += n * (fp32 ? (8 + 8 + 4) : 16);
                     if (g.mode == SEG_ACC_SET) b += n * 8;

@@ -38,9 +38,12 @@ def depth(d):
 
 
 class Coast:
+    """Sinuous coastline; the sine amplitudes scale with the basin length so the
+    coast keeps the same slopes (at most about 0.5) for any Ly."""
+
     def __init__(self, Lx, Ly, x_off, rng):
         self.Lx, self.Ly, self.x_off = Lx, Ly, x_off
-        self.a = rng.uniform(20e3, 60e3, 3)
+        self.a = rng.uniform(20e3, 60e3, 3) * min(1.0, Ly / 9600e3)
         self.k = rng.integers(2, 13, 3)
         self.phi = rng.uniform(0, 2 * np.pi, 3)
 
@@ -158,6 +161,16 @@ def basin_case(Ly=9600e3, Lx=1500e3, x_off=150e3, dx_min=500.0, dx_max=20e3, d0=
     nb = full.cellsOnCell
     wet_nb = (np.where(nb >= 0, ocean[np.maximum(nb, 0)], False)).any(1)
     ocean &= wet_nb
+    # every kept vertex needs a positive area from its kept cells: drop the
+    # kept cells of a vertex whose kites (obtuse triangles) sum to <= 0
+    for _ in range(10):
+        cov = full.cellsOnVertex
+        kept = ocean[cov]
+        av = np.where(kept, full.kiteAreasOnVertex, 0.0).sum(1)
+        bad = kept.any(1) & (av <= 0.0)
+        if not bad.any():
+            break
+        ocean[cov[bad][kept[bad]]] = False
     mesh = finalize(apply_cell_mask(full, ocean))
     if verbose:
         print(f"basin: {mesh.nCells} cells {mesh.nEdges} edges {mesh.nVertices} vertices, {time.time() - t0:.1f}s")
