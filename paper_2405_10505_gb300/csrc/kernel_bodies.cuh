@@ -44,13 +44,13 @@ struct VertArgs {
 struct PrepArgs {
     int lo, hi;
     const double *u_in, *hst, *q;
-    double *Fe, *qe;
+    double *Fe, *qe, *FQ;
 };
 
 struct EdgeArgs {
     SegSet segs;
     int lo, hi;
-    const double *u_in, *hst, *K, *Fe, *qe, *u0;
+    const double *u_in, *hst, *K, *Fe, *qe, *FQ, *u0;
     double *us_out, *u_state, *acc;
     double cdt, g;
 };
@@ -88,7 +88,7 @@ inline VertArgs vert_args(const Op &op, const DevArrays &arr) {
 }
 
 inline PrepArgs prep_args(const Op &op, const DevArrays &arr) {
-    return PrepArgs{op.lo, op.hi, arr.a[op.in_u], arr.a[op.hst], arr.a[A_Q], arr.a[A_FE], arr.a[A_QE]};
+    return PrepArgs{op.lo, op.hi, arr.a[op.in_u], arr.a[op.hst], arr.a[A_Q], arr.a[A_FE], arr.a[A_QE], arr.a[A_FQ]};
 }
 
 inline EdgeArgs edge_args(const Op &op, const DevArrays &arr, double g) {
@@ -96,7 +96,7 @@ inline EdgeArgs edge_args(const Op &op, const DevArrays &arr, double g) {
     EdgeArgs a;
     a.segs = segs_of(op);
     a.lo = op.lo; a.hi = op.hi;
-    a.u_in = A[op.in_u]; a.hst = A[op.hst]; a.K = A[A_K]; a.Fe = A[A_FE]; a.qe = A[A_QE];
+    a.u_in = A[op.in_u]; a.hst = A[op.hst]; a.K = A[A_K]; a.Fe = A[A_FE]; a.qe = A[A_QE]; a.FQ = A[A_FQ];
     a.u0 = A[op.u0]; a.us_out = A[op.out_u]; a.u_state = A[A_U]; a.acc = A[A_ACCU];
     a.cdt = op.cdt; a.g = g;
     return a;
@@ -137,7 +137,7 @@ FB_HD void cell_body(const DevMesh &m, const CellArgs &a, int i) {
         ke += m.cKE[j * nC + i] * ue * ue;
         if (mode != SEG_KONLY) {
             const int nb = m.coc[j * nC + i];
-            psi += m.cDiv[j * nC + i] * (0.5 * (hi_ + a.h_in[nb]) * ue);
+            psi += (0.5 * m.cDiv[j * nC + i]) * ((hi_ + a.h_in[nb]) * ue);
         }
     }
     a.K[i] = ke;
@@ -173,19 +173,23 @@ FB_UNROLL
     a.q[v] = (z + m.fV[v]) / hv;
 }
 
-// Edge e: thickness flux F_e = h_e u_e (zero on no-flow edges) and the edge
-// PV q_e = (q_v0 + q_v1) / 2.
+// Edge e: thickness flux F_e = h_e u_e (zero on no-flow edges), the edge PV
+// q_e = (q_v0 + q_v1) / 2 and their product F_e q_e.
 FB_HD void prep_body(const DevMesh &m, const PrepArgs &a, int e) {
     const int c0 = m.coe0[e], c1 = m.coe1[e];
-    a.Fe[e] = m.ebnd[e] ? 0.0 : 0.5 * (a.hst[c0] + a.hst[c1]) * a.u_in[e];
-    a.qe[e] = 0.5 * (a.q[m.voe0[e]] + a.q[m.voe1[e]]);
+    const double F = m.ebnd[e] ? 0.0 : 0.5 * (a.hst[c0] + a.hst[c1]) * a.u_in[e];
+    const double q = 0.5 * (a.q[m.voe0[e]] + a.q[m.voe1[e]]);
+    a.Fe[e] = F;
+    a.qe[e] = q;
+    a.FQ[e] = F * q;
 }
 
 // Edge e: Phi_e = sum_j w_j F_{e_j} (q_e + q_{e_j}) / 2
 //                 - [K_c1 - K_c0 + g (xi_c1 - xi_c0)] / d_e  (+ forcing)
 // (rotating SWE, Eq. nonlinear_swe, in TRiSK form; forcing of Eq.
 // hurricane_model), then the stage update u_s = u0 + c tau Phi or the
-// correction sum of Eq. if_correction.
+// correction sum of Eq. if_correction.  The Coriolis sum is taken as
+// (q_e sum_j w_j F_j + sum_j w_j F_j q_j) / 2: two FMAs per neighbour.
 template <bool FORCING>
 FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, int e) {
     const int mode = seg_mode(a.segs, e);
@@ -196,24 +200,26 @@ FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, 
         const int c0 = m.coe0[e], c1 = m.coe1[e];
         const int n = m.nEoE[e];
         const double qself = a.qe[e];
-        double cor = 0.0, vt = 0.0;
+        double sF = 0.0, sG = 0.0, vt = 0.0;
         for (int j = 0; j < n; ++j) {
             const int x = m.eoe[j * nE + e];
             const double w = m.woe[j * nE + e];
-            cor += w * a.Fe[x] * (0.5 * (qself + a.qe[x]));
+            sF += w * a.Fe[x];
+            sG += w * a.FQ[x];
             if (FORCING) vt += w * a.u_in[x];
         }
+        const double cor = 0.5 * (qself * sF + sG);
         const double h0c = a.hst[c0], h1c = a.hst[c1];
         const double grad = (a.K[c1] - a.K[c0]) + a.g * ((h1c + m.bottom[c1]) - (h0c + m.bottom[c0]));
         phi = cor - grad * m.invDc[e];
         if (FORCING) {
             const double ue = a.u_in[e];
-            const double he = 0.5 * (h0c + h1c);
+            const double rhe = 2.0 / (h0c + h1c);
             if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
                 const double dn = fz.windN[e] - ue, dt = fz.windT[e] - vt;
-                phi += fz.cw[e] * sqrt(dn * dn + dt * dt) * dn / he;
+                phi += fz.cw[e] * sqrt(dn * dn + dt * dt) * dn * rhe;
             }
-            if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= fz.cd * sqrt(ue * ue + vt * vt) * ue / he;
+            if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= fz.cd * sqrt(ue * ue + vt * vt) * ue * rhe;
             if (fz.flags & FBLTS_FORCE_VORTEX) phi -= (fz.ps[c1] - fz.ps[c0]) * m.invDc[e] / fz.rho0;
         }
     }

@@ -107,45 +107,73 @@ inline IfArgs32 if_args32(const Op &op, const DevArrays &arr, const DevMesh &m) 
 }
 
 // Cell i, FP32 tendency: the edge flux F_e = (H_e + (xi_i + xi_nb)/2) u_e in
-// float (bit-identical from both cells of the edge: the sums commute), the
-// divergence Psi_i = -(1/A_i) sum_j n_{e,i} l_e F_e accumulated in double
-// from the float products l_e F_e (exact in double and the same from both
-// cells), so the fluxes of an edge cancel in sum_i A_i h_i to double roundoff
-// (Eq. trisk_thickness, Theorem 1); K_i = (1/A_i) sum_j (d_e l_e / 4) u_e^2;
-// the stage value xi_s = xi0 + c tau Psi, in place h += c tau Psi in double
-// (Eq. fbrk32), and the FB average in xi.
+// float (bit-identical from both cells of the edge: the sums commute) and
+// Psi_i = -(1/A_i) sum_j n_{e,i} l_e F_e (Eq. trisk_thickness).  Stage values
+// (xi_s = xi0 + c tau Psi) take the float sum.  Where the double time level
+// or a correction sum changes, the sum is taken in double from the products
+// l_e F_e (exact in double and the same from both cells), so the fluxes of an
+// edge cancel in sum_i A_i h_i to double roundoff (Theorem 1).  K_i =
+// (1/A_i) sum_j (d_e l_e / 4) u_e^2.  NMAX bounds the edges of a cell so the
+// row is loaded before the dependent gathers.
+template <int NMAX>
 FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     const int mode = seg_mode(a.segs, i);
     if (mode == SEG_NONE) return;
     const int n = m.nEoC[i];
     const int nC = m.nC;
-    double S = 0.0;
-    float ke = 0.f;
-    const float xi_i = a.xi_in[i];
-    const float H_i = m.H32[i];
-    for (int j = 0; j < n; ++j) {
-        const int v = m.eocS[j * nC + i];
-        const int e = v < 0 ? ~v : v;
-        const float ue = a.u_in[e];
-        ke += m.ke32[e] * ue * ue;
-        if (mode != SEG_KONLY) {
-            const int nb = m.coc[j * nC + i];
-            const float he = 0.5f * (H_i + m.H32[nb]) + 0.5f * (xi_i + a.xi_in[nb]);
-            const float F = he * ue;
-            // n_{e,i} = +1 for the first cell: its outflow lowers h
-            S = fma(v < 0 ? (double)m.dv32[e] : -(double)m.dv32[e], (double)F, S);
+    int er[NMAX], nb[NMAX];
+    FB_UNROLL
+    for (int j = 0; j < NMAX; ++j) {
+        er[j] = 0;
+        nb[j] = i;
+        if (j < n) {
+            er[j] = m.eocS[j * nC + i];
+            nb[j] = m.coc[j * nC + i];
         }
     }
+    float ue[NMAX], sdv[NMAX], kw[NMAX];
+    FB_UNROLL
+    for (int j = 0; j < NMAX; ++j) {
+        ue[j] = 0.f;
+        sdv[j] = 0.f;
+        kw[j] = 0.f;
+        if (j < n) {
+            const int e = er[j] < 0 ? ~er[j] : er[j];
+            ue[j] = a.u_in[e];
+            kw[j] = m.ke32[e];
+            const float dv = m.dv32[e];
+            sdv[j] = er[j] < 0 ? dv : -dv;    // -n_{e,i} l_e
+        }
+    }
+    float ke = 0.f;
+    FB_UNROLL
+    for (int j = 0; j < NMAX; ++j) ke += kw[j] * ue[j] * ue[j];
     const double invA = m.invA[i];
     a.K[i] = ke * (float)invA;
+    if (mode == SEG_KONLY) return;
+    const float xi_i = a.xi_in[i];
+    const float H_i = m.H32[i];
+    float F[NMAX];
+    FB_UNROLL
+    for (int j = 0; j < NMAX; ++j) {
+        const float he = 0.5f * (H_i + m.H32[nb[j]]) + 0.5f * (xi_i + a.xi_in[nb[j]]);
+        F[j] = he * ue[j];
+    }
+    if (mode == SEG_UPD) {
+        float S = 0.f;
+        FB_UNROLL
+        for (int j = 0; j < NMAX; ++j) S += sdv[j] * F[j];
+        const float x0 = a.xi0[i];
+        const float xn = x0 + (float)a.cdt * (S * (float)invA);
+        a.xi_out[i] = xn;
+        a.hst_out[i] = a.fb_a * xn + a.fb_b * a.xiprev[i] + a.fb_c * x0;
+        return;
+    }
+    double S = 0.0;
+    FB_UNROLL
+    for (int j = 0; j < NMAX; ++j) S = fma((double)sdv[j], (double)F[j], S);
     const double psi = S * invA;
     switch (mode) {
-        case SEG_UPD: {
-            const float x0 = a.xi0[i];
-            const float xn = x0 + (float)(a.cdt * psi);
-            a.xi_out[i] = xn;
-            a.hst_out[i] = a.fb_a * xn + a.fb_b * a.xiprev[i] + a.fb_c * x0;
-        } break;
         case SEG_INPLACE: {
             const float x0 = a.xi0[i];
             const double hn = a.h_state[i] + a.cdt * psi;
@@ -182,7 +210,7 @@ FB_HD void prep32_body(const DevMesh &m, const PrepArgs32 &a, int e) {
 // Edge e: Phi_e in float (the pressure gradient g (xi_c1 - xi_c0) / d_e needs
 // no cancellation of large depths), stage value u_s = u0 + c tau Phi, in
 // place u += c tau Phi in double, or the correction sum in double.
-template <bool FORCING>
+template <bool FORCING, int NMAX>
 FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &fz, int e) {
     const int mode = seg_mode(a.segs, e);
     if (mode == SEG_NONE) return;
@@ -194,24 +222,35 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
         const float qself = a.qe[e];
         float cor = 0.f, vt = 0.f;
         if (m.rows) {
-            // neighbours = the other edges of c0 then of c1, from the cells' rows
+            // neighbours = the other edges of c0 then of c1, from the cells' rows:
+            // the row indices and weights are loaded before the dependent gathers
             const int nC = m.nC;
             const unsigned short sl = m.eslot[e];
-            int k = 0;
+            int k0 = 0;
             for (int side = 0; side < 2; ++side) {
                 const int c = side ? c1 : c0;
                 const int nc = m.nEoC[c];
                 const int p = side ? (sl >> 8) : (sl & 0xff);
-                for (int j = 1; j < nc; ++j) {
-                    int jj = p + j;
-                    if (jj >= nc) jj -= nc;
-                    const int xs = m.eocS[jj * nC + c];
-                    const int x = xs < 0 ? ~xs : xs;
-                    const float w = m.woeC32[k * nE + e];
-                    ++k;
-                    cor += w * a.Fe[x] * (0.5f * (qself + a.qe[x]));
-                    if (FORCING) vt += w * a.u_in[x];
+                int xs[NMAX - 1];
+                float w[NMAX - 1];
+                FB_UNROLL
+                for (int j = 1; j < NMAX; ++j) {
+                    xs[j - 1] = e;
+                    w[j - 1] = 0.f;
+                    if (j < nc) {
+                        int jj = p + j;
+                        if (jj >= nc) jj -= nc;
+                        const int v = m.eocS[jj * nC + c];
+                        xs[j - 1] = v < 0 ? ~v : v;
+                        w[j - 1] = m.woeC32[(k0 + j - 1) * nE + e];
+                    }
                 }
+                FB_UNROLL
+                for (int j = 0; j < NMAX - 1; ++j) {
+                    cor += w[j] * a.Fe[xs[j]] * (0.5f * (qself + a.qe[xs[j]]));
+                    if (FORCING) vt += w[j] * a.u_in[xs[j]];
+                }
+                k0 += nc - 1;
             }
         } else {
             for (int j = 0; j < n; ++j) {

@@ -54,9 +54,10 @@ __global__ void __launch_bounds__(TPB) forcing_pass(DevMesh m, DevForcing fz) {
     forcing_body(m, fz, time, t);
 }
 
+template <int NMAX>
 __global__ void __launch_bounds__(TPB) cell32_pass(DevMesh m, CellArgs32 a) {
     const int i = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.hi) cell32_body(m, a, i);
+    if (i < a.hi) cell32_body<NMAX>(m, a, i);
 }
 
 __global__ void __launch_bounds__(TPB) vert32_pass(DevMesh m, VertArgs32 a) {
@@ -69,11 +70,12 @@ __global__ void __launch_bounds__(TPB) eprep32_pass(DevMesh m, PrepArgs32 a) {
     if (e < a.hi) prep32_body(m, a, e);
 }
 
-template <bool FORCING>
+template <bool FORCING, int NMAX>
 __global__ void __launch_bounds__(TPB) edge32_pass(DevMesh m, EdgeArgs32 a, DevForcing fz) {
     const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < a.hi) edge32_body<FORCING>(m, a, fz, e);
+    if (e < a.hi) edge32_body<FORCING, NMAX>(m, a, fz, e);
 }
+
 
 __global__ void __launch_bounds__(TPB) save32_pass(IfArgs32 a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -194,10 +196,13 @@ inline int nblk(long long n) { return (int)((n + TPB - 1) / TPB); }
 static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &arr, const DevForcing &fz,
                                double g, long long *step_counter, cudaStream_t st) {
     switch (op.kind) {
-        case OP_CELL:
+        case OP_CELL: {
             if (op.hi <= op.lo) return cudaSuccess;
-            cell32_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, cell_args32(op, arr, m));
-            break;
+            const CellArgs32 a = cell_args32(op, arr, m);
+            if (m.maxE <= 6) cell32_pass<6><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, a);
+            else if (m.maxE <= 8) cell32_pass<8><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, a);
+            else cell32_pass<12><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, a);
+        } break;
         case OP_VERT:
             if (op.hi <= op.lo) return cudaSuccess;
             vert32_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, vert_args32(op, arr));
@@ -206,11 +211,21 @@ static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &
             if (op.hi <= op.lo) return cudaSuccess;
             eprep32_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, prep_args32(op, arr));
             break;
-        case OP_EDGE:
+        case OP_EDGE: {
             if (op.hi <= op.lo) return cudaSuccess;
-            if (fz.flags) edge32_pass<true><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, edge_args32(op, arr, g), fz);
-            else edge32_pass<false><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, edge_args32(op, arr, g), fz);
-            break;
+            const EdgeArgs32 a = edge_args32(op, arr, g);
+            const int nb = nblk(op.hi - op.lo);
+            if (m.maxE <= 6) {
+                if (fz.flags) edge32_pass<true, 6><<<nb, TPB, 0, st>>>(m, a, fz);
+                else edge32_pass<false, 6><<<nb, TPB, 0, st>>>(m, a, fz);
+            } else if (m.maxE <= 8) {
+                if (fz.flags) edge32_pass<true, 8><<<nb, TPB, 0, st>>>(m, a, fz);
+                else edge32_pass<false, 8><<<nb, TPB, 0, st>>>(m, a, fz);
+            } else {
+                if (fz.flags) edge32_pass<true, 12><<<nb, TPB, 0, st>>>(m, a, fz);
+                else edge32_pass<false, 12><<<nb, TPB, 0, st>>>(m, a, fz);
+            }
+        } break;
         case OP_SAVE:
         case OP_PRED:
         case OP_FINAL: {

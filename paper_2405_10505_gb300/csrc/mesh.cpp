@@ -91,7 +91,7 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
         set_error("mesh_create: nLevels > 1 needs ltsLevel and M");
         return FBLTS_E_ARG;
     }
-    hm.nC = nC; hm.nE = nE; hm.nV = nV; hm.maxE = mE; hm.maxE2 = mE2; hm.L = L;
+    hm.nC = nC; hm.nE = nE; hm.nV = nV; hm.L = L;
     hm.nIF1 = d->nIF1Layers > 0 ? d->nIF1Layers : 2;
     hm.nIF2 = d->nIF2Layers > 0 ? d->nIF2Layers : 2;
     hm.kin_cap = hm.nIF1 + hm.nIF2 + 3;
@@ -154,6 +154,14 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
             set_error("mesh_create: edge %d listed by %d cells", e, listed[e]);
             return FBLTS_E_MESH;
         }
+    // row widths of the library's own arrays: the actual maxima (at most 12 edges per cell)
+    int W = 3, W2 = 1;
+    for (int i = 0; i < nC; ++i) W = std::max(W, d->nEdgesOnCell[i]);
+    for (int e = 0; e < nE; ++e) W2 = std::max(W2, d->nEdgesOnEdge[e]);
+    if (W > 12) { set_error("mesh_create: a cell has %d edges (at most 12)", W); return FBLTS_E_MESH; }
+    W2 = std::max(W2, 2 * (W - 1));
+    hm.maxE = W;
+    hm.maxE2 = W2;
     std::vector<int> eov(3 * (size_t)nV, -1);
     if (d->edgesOnVertex) {
         for (size_t k = 0; k < 3 * (size_t)nV; ++k) {
@@ -355,8 +363,8 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
 
     // ---------------------------------------------------------- new-order arrays
     const auto &c2n = hm.cell_o2n, &e2n = hm.edge_o2n, &v2n = hm.vert_o2n;
-    hm.nEoC.resize(nC); hm.eoc.assign((size_t)nC * mE, 0); hm.coc.assign((size_t)nC * mE, 0);
-    hm.cDiv.assign((size_t)nC * mE, 0.0); hm.cKE.assign((size_t)nC * mE, 0.0);
+    hm.nEoC.resize(nC); hm.eoc.assign((size_t)nC * W, 0); hm.coc.assign((size_t)nC * W, 0);
+    hm.cDiv.assign((size_t)nC * W, 0.0); hm.cKE.assign((size_t)nC * W, 0.0);
     hm.area.resize(nC);
     for (int i = 0; i < nC; ++i) {
         int io = hm.cell_n2o[i];
@@ -366,7 +374,7 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
         hm.area[i] = A;
         for (int j = 0; j < n; ++j) {
             int eo = d->edgesOnCell[(size_t)io * mE + j];
-            size_t k = (size_t)i * mE + j;
+            size_t k = (size_t)i * W + j;
             hm.eoc[k] = e2n[eo];
             if (ebnd[eo]) {
                 hm.coc[k] = i;
@@ -378,14 +386,14 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
             hm.cDiv[k] = -sgn * d->dvEdge[eo] / A;
             hm.cKE[k] = 0.25 * d->dcEdge[eo] * d->dvEdge[eo] / A;
         }
-        for (int j = n; j < mE; ++j) {  // padding: harmless entries
-            size_t k = (size_t)i * mE + j;
-            hm.eoc[k] = hm.eoc[(size_t)i * mE];
+        for (int j = n; j < W; ++j) {  // padding: harmless entries
+            size_t k = (size_t)i * W + j;
+            hm.eoc[k] = hm.eoc[(size_t)i * W];
             hm.coc[k] = i;
         }
     }
     hm.coe.resize(2 * (size_t)nE); hm.voe.resize(2 * (size_t)nE); hm.ebnd.resize(nE);
-    hm.nEoE.resize(nE); hm.eoe.assign((size_t)nE * mE2, 0); hm.woe.assign((size_t)nE * mE2, 0.0);
+    hm.nEoE.resize(nE); hm.eoe.assign((size_t)nE * W2, 0); hm.woe.assign((size_t)nE * W2, 0.0);
     hm.invDc.resize(nE);
     hm.has_angle = d->angleEdge != nullptr;
     hm.has_xy_cell = d->xCell && d->yCell;
@@ -412,10 +420,10 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
         int ne = ebnd[eo] ? 0 : d->nEdgesOnEdge[eo];
         hm.nEoE[e] = ne;
         for (int j = 0; j < ne; ++j) {
-            hm.eoe[(size_t)e * mE2 + j] = e2n[d->edgesOnEdge[(size_t)eo * mE2 + j]];
-            hm.woe[(size_t)e * mE2 + j] = d->weightsOnEdge[(size_t)eo * mE2 + j];
+            hm.eoe[(size_t)e * W2 + j] = e2n[d->edgesOnEdge[(size_t)eo * mE2 + j]];
+            hm.woe[(size_t)e * W2 + j] = d->weightsOnEdge[(size_t)eo * mE2 + j];
         }
-        for (int j = ne; j < mE2; ++j) hm.eoe[(size_t)e * mE2 + j] = e;
+        for (int j = ne; j < W2; ++j) hm.eoe[(size_t)e * W2 + j] = e;
         if (hm.has_angle) { hm.cosE[e] = std::cos(d->angleEdge[eo]); hm.sinE[e] = std::sin(d->angleEdge[eo]); }
         if (hm.has_xy_edge) { hm.xE[e] = d->xEdge[eo]; hm.yE[e] = d->yEdge[eo]; }
     }
@@ -450,13 +458,13 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
         }
     }
     // signed edge rows and per-edge metrics of the FP32 cell pass
-    hm.eocS.assign((size_t)nC * mE, 0);
+    hm.eocS.assign((size_t)nC * W, 0);
     hm.invA.resize(nC);
     for (int i = 0; i < nC; ++i) {
         hm.invA[i] = 1.0 / hm.area[i];
-        for (int j = 0; j < mE; ++j) {
-            const int e = hm.eoc[(size_t)i * mE + j];
-            hm.eocS[(size_t)i * mE + j] = (j < hm.nEoC[i] && !hm.ebnd[e] && hm.coe[2 * e + 1] == i) ? ~e : e;
+        for (int j = 0; j < W; ++j) {
+            const int e = hm.eoc[(size_t)i * W + j];
+            hm.eocS[(size_t)i * W + j] = (j < hm.nEoC[i] && !hm.ebnd[e] && hm.coe[2 * e + 1] == i) ? ~e : e;
         }
     }
     hm.dvE.assign(nE, 0.0);
@@ -469,8 +477,8 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
     }
     // neighbour edges as the two cells' edge rows (see HostMesh::rows_canonical)
     hm.eslot.assign(nE, 0);
-    hm.woeC.assign((size_t)nE * mE2, 0.0);
-    hm.rows_canonical = mE <= 255 && 2 * (mE - 1) <= mE2;
+    hm.woeC.assign((size_t)nE * W2, 0.0);
+    hm.rows_canonical = true;
     for (int e = 0; e < nE && hm.rows_canonical; ++e) {
         if (hm.ebnd[e]) continue;
         int k = 0, matched = 0;
@@ -479,15 +487,15 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
             const int c = hm.coe[2 * e + side];
             const int n = hm.nEoC[c];
             int p = -1;
-            for (int j = 0; j < n; ++j) if (hm.eoc[(size_t)c * mE + j] == e) p = j;
+            for (int j = 0; j < n; ++j) if (hm.eoc[(size_t)c * W + j] == e) p = j;
             if (p < 0) { hm.rows_canonical = false; break; }
             slot[side] = p;
             for (int j = 1; j < n; ++j) {
-                const int x = hm.eoc[(size_t)c * mE + (p + j) % n];
+                const int x = hm.eoc[(size_t)c * W + (p + j) % n];
                 double w = 0.0;
                 for (int q = 0; q < hm.nEoE[e]; ++q)
-                    if (hm.eoe[(size_t)e * mE2 + q] == x) { w = hm.woe[(size_t)e * mE2 + q]; ++matched; }
-                hm.woeC[(size_t)e * mE2 + k++] = w;
+                    if (hm.eoe[(size_t)e * W2 + q] == x) { w = hm.woe[(size_t)e * W2 + q]; ++matched; }
+                hm.woeC[(size_t)e * W2 + k++] = w;
             }
         }
         if (!hm.rows_canonical) break;

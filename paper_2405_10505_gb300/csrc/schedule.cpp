@@ -277,7 +277,7 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
                 b = (double)(op.hi - op.lo) * (3 * (4 + 4 + C + C) + C + (fp32 ? 4 : 0) + 1.5 * R + 0.5 * R + R);
                 break;
             case OP_EPREP:
-                b = (double)(op.hi - op.lo) * (17 + (fp32 ? 4 : 0) + R + R * 2 * cpe + R * 2 * vpe + 2 * R);
+                b = (double)(op.hi - op.lo) * (17 + (fp32 ? 4 : 0) + R + R * 2 * cpe + R * 2 * vpe + (fp32 ? 2 : 3) * R);
                 break;
             case OP_EDGE:
                 for (int k = 0; k < op.nseg; ++k) {
