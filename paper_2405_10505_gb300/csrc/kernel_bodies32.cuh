@@ -156,8 +156,11 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     float F[NMAX];
     FB_UNROLL
     for (int j = 0; j < NMAX; ++j) {
-        const float he = 0.5f * (H_i + m.H32[nb[j]]) + 0.5f * (xi_i + a.xi_in[nb[j]]);
-        F[j] = he * ue[j];
+        F[j] = 0.f;
+        if (j < n) {
+            const float he = 0.5f * (H_i + m.H32[nb[j]]) + 0.5f * (xi_i + a.xi_in[nb[j]]);
+            F[j] = he * ue[j];
+        }
     }
     if (mode == SEG_UPD) {
         float S = 0.f;
@@ -247,8 +250,10 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
                 }
                 FB_UNROLL
                 for (int j = 0; j < NMAX - 1; ++j) {
-                    cor += w[j] * a.Fe[xs[j]] * (0.5f * (qself + a.qe[xs[j]]));
-                    if (FORCING) vt += w[j] * a.u_in[xs[j]];
+                    if (j < nc - 1) {
+                        cor += w[j] * a.Fe[xs[j]] * (0.5f * (qself + a.qe[xs[j]]));
+                        if (FORCING) vt += w[j] * a.u_in[xs[j]];
+                    }
                 }
                 k0 += nc - 1;
             }
