@@ -357,7 +357,10 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     auto is_double = [&](int a) {
         return !f32 || a == A_H || a == A_U || a == A_ACCH || a == A_ACCU || a == A_SH0 || a == A_SU0;
     };
-    auto count = [&](int a) -> size_t { return arr_is_cell(a) ? (size_t)nC : (arr_is_vert(a) ? (size_t)nV : (size_t)nE); };
+    auto count = [&](int a) -> size_t {
+        if (a == A_FQU) return 4 * (size_t)nE;   // {F, q_e, u, 0} per edge (FP32 path)
+        return arr_is_cell(a) ? (size_t)nC : (arr_is_vert(a) ? (size_t)nV : (size_t)nE);
+    };
     // every allocation in order; the sizing pass and the carving pass walk the same list
     size_t szc = sizeof(double) * (size_t)nC, sze = sizeof(double) * (size_t)nE;
     std::vector<size_t> plan;
@@ -367,6 +370,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     if (f32) {
         plan.push_back(4 * (size_t)nC); plan.push_back(4 * (size_t)nE);            // shadows
         plan.push_back(4 * (size_t)nC); plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nV);  // depths
+        plan.push_back(16 * (size_t)nE);                                            // per-edge record
         plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nE);
         plan.push_back(4 * (size_t)nC);                                             // forcing (float)
     }
@@ -407,12 +411,14 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     s->fz.cw = (double *)got[gi++];
     s->fz.ps = (double *)got[gi++];
     float *H32 = nullptr, *He32 = nullptr, *Hv32 = nullptr;
+    float4 *estat = nullptr;
     if (f32) {
         s->arr.xi32 = (float *)got[gi++];
         s->arr.u32 = (float *)got[gi++];
         H32 = (float *)got[gi++];
         He32 = (float *)got[gi++];
         Hv32 = (float *)got[gi++];
+        estat = (float4 *)got[gi++];
         s->fz.windN32 = (float *)got[gi++];
         s->fz.windT32 = (float *)got[gi++];
         s->fz.cw32 = (float *)got[gi++];
@@ -440,8 +446,8 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         }
     }
     if (st == FBLTS_OK && f32) {
-        s->dm.H32 = H32; s->dm.He32 = He32; s->dm.Hv32 = Hv32;
-        if (launch_fp32_depths(s->dm, H32, He32, Hv32, s->st) != cudaSuccess ||
+        s->dm.H32 = H32; s->dm.He32 = He32; s->dm.Hv32 = Hv32; s->dm.estat = estat;
+        if (launch_fp32_depths(s->dm, H32, He32, Hv32, estat, s->st) != cudaSuccess ||
             launch_fp32_shadows(s->dm, s->arr, s->st) != cudaSuccess) {
             set_error("state_init: FP32 setup failed");
             st = FBLTS_E_CUDA;

@@ -80,7 +80,7 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm);
 // Device arrays of a state, addressed by id in the schedule.
 enum Arr : int {
     A_H = 0, A_U, A_HS1, A_HS2, A_HS3, A_HST1, A_HST2, A_HST3, A_US1, A_US2, A_US3,
-    A_K, A_Q, A_FE, A_QE, A_FQ, A_ACCH, A_ACCU,
+    A_K, A_Q, A_FE, A_QE, A_FQ, A_FQU, A_ACCH, A_ACCU,
     A_SH0, A_SH1, A_SH2, A_SH3, A_SU0, A_SU1, A_SU2, A_SU3,
     A_COUNT
 };

@@ -27,13 +27,14 @@ struct VertArgs32 {
 struct PrepArgs32 {
     int lo, hi;
     const float *u_in, *hst, *q;
-    float *Fe, *qe;
+    float4 *fqu;      // per edge {F_e, q_e, u_e, 0}
 };
 
 struct EdgeArgs32 {
     SegSet segs;
     int lo, hi;
-    const float *u_in, *hst, *K, *Fe, *qe, *u0;
+    const float *u_in, *hst, *K, *u0;
+    const float4 *fqu;
     float *us_out, *u_shadow;
     double *u_state, *acc;
     double cdt;
@@ -75,14 +76,14 @@ inline VertArgs32 vert_args32(const Op &op, const DevArrays &arr) {
 }
 
 inline PrepArgs32 prep_args32(const Op &op, const DevArrays &arr) {
-    return PrepArgs32{op.lo, op.hi, f_in(arr, op.in_u), arr.f[op.hst], arr.f[A_Q], arr.f[A_FE], arr.f[A_QE]};
+    return PrepArgs32{op.lo, op.hi, f_in(arr, op.in_u), arr.f[op.hst], arr.f[A_Q], (float4 *)arr.f[A_FQU]};
 }
 
 inline EdgeArgs32 edge_args32(const Op &op, const DevArrays &arr, double g) {
     EdgeArgs32 a;
     a.segs = segs_of(op);
     a.lo = op.lo; a.hi = op.hi;
-    a.u_in = f_in(arr, op.in_u); a.hst = arr.f[op.hst]; a.K = arr.f[A_K]; a.Fe = arr.f[A_FE]; a.qe = arr.f[A_QE];
+    a.u_in = f_in(arr, op.in_u); a.hst = arr.f[op.hst]; a.K = arr.f[A_K]; a.fqu = (const float4 *)arr.f[A_FQU];
     a.u0 = f_in(arr, op.u0); a.us_out = arr.f[op.out_u]; a.u_shadow = arr.u32;
     a.u_state = arr.a[A_U]; a.acc = arr.a[A_ACCU];
     a.cdt = op.cdt; a.g = (float)g;
@@ -107,14 +108,16 @@ inline IfArgs32 if_args32(const Op &op, const DevArrays &arr, const DevMesh &m) 
 }
 
 // Cell i, FP32 tendency: the edge flux F_e = (H_e + (xi_i + xi_nb)/2) u_e in
-// float (bit-identical from both cells of the edge: the sums commute) and
+// float (bit-identical from both cells of the edge: H_e is per edge and the
+// sum commutes) and
 // Psi_i = -(1/A_i) sum_j n_{e,i} l_e F_e (Eq. trisk_thickness).  Stage values
 // (xi_s = xi0 + c tau Psi) take the float sum.  Where the double time level
 // or a correction sum changes, the sum is taken in double from the products
 // l_e F_e (exact in double and the same from both cells), so the fluxes of an
 // edge cancel in sum_i A_i h_i to double roundoff (Theorem 1).  K_i =
 // (1/A_i) sum_j (d_e l_e / 4) u_e^2.  NMAX bounds the edges of a cell so the
-// row is loaded before the dependent gathers.
+// row is loaded before the dependent gathers; the static per-edge data
+// {l_e, d_e l_e / 4, H_e} is one 16-byte gather.
 template <int NMAX>
 FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     const int mode = seg_mode(a.segs, i);
@@ -131,18 +134,20 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
             nb[j] = m.coc[j * nC + i];
         }
     }
-    float ue[NMAX], sdv[NMAX], kw[NMAX];
+    float ue[NMAX], sdv[NMAX], kw[NMAX], He[NMAX];
     FB_UNROLL
     for (int j = 0; j < NMAX; ++j) {
         ue[j] = 0.f;
         sdv[j] = 0.f;
         kw[j] = 0.f;
+        He[j] = 0.f;
         if (j < n) {
             const int e = er[j] < 0 ? ~er[j] : er[j];
             ue[j] = a.u_in[e];
-            kw[j] = m.ke32[e];
-            const float dv = m.dv32[e];
-            sdv[j] = er[j] < 0 ? dv : -dv;    // -n_{e,i} l_e
+            const float4 st = m.estat[e];
+            kw[j] = st.y;
+            He[j] = st.z;
+            sdv[j] = er[j] < 0 ? st.x : -st.x;    // -n_{e,i} l_e
         }
     }
     float ke = 0.f;
@@ -152,16 +157,9 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     a.K[i] = ke * (float)invA;
     if (mode == SEG_KONLY) return;
     const float xi_i = a.xi_in[i];
-    const float H_i = m.H32[i];
     float F[NMAX];
     FB_UNROLL
-    for (int j = 0; j < NMAX; ++j) {
-        F[j] = 0.f;
-        if (j < n) {
-            const float he = 0.5f * (H_i + m.H32[nb[j]]) + 0.5f * (xi_i + a.xi_in[nb[j]]);
-            F[j] = he * ue[j];
-        }
-    }
+    for (int j = 0; j < NMAX; ++j) F[j] = (He[j] + 0.5f * (xi_i + a.xi_in[nb[j]])) * ue[j];
     if (mode == SEG_UPD) {
         float S = 0.f;
         FB_UNROLL
@@ -203,17 +201,19 @@ FB_HD void vert32_body(const DevMesh &m, const VertArgs32 &a, int v) {
     a.q[v] = (z + m.fV32[v]) / (m.Hv32[v] + xv);
 }
 
-// Edge e: F_e = (H_e + (xi_c0 + xi_c1)/2) u_e and q_e.
+// Edge e: {F_e = (H_e + (xi_c0 + xi_c1)/2) u_e, q_e, u_e} as one 16-byte
+// record, so the edge pass gathers a neighbour with one load.
 FB_HD void prep32_body(const DevMesh &m, const PrepArgs32 &a, int e) {
     const int c0 = m.coe0[e], c1 = m.coe1[e];
-    a.Fe[e] = m.ebnd[e] ? 0.f : (m.He32[e] + 0.5f * (a.hst[c0] + a.hst[c1])) * a.u_in[e];
-    a.qe[e] = 0.5f * (a.q[m.voe0[e]] + a.q[m.voe1[e]]);
+    const float ue = a.u_in[e];
+    const float F = m.ebnd[e] ? 0.f : (m.He32[e] + 0.5f * (a.hst[c0] + a.hst[c1])) * ue;
+    a.fqu[e] = make_float4(F, 0.5f * (a.q[m.voe0[e]] + a.q[m.voe1[e]]), ue, 0.f);
 }
 
 // Edge e: Phi_e in float (the pressure gradient g (xi_c1 - xi_c0) / d_e needs
 // no cancellation of large depths), stage value u_s = u0 + c tau Phi, in
 // place u += c tau Phi in double, or the correction sum in double.
-template <bool FORCING, int NMAX>
+template <bool FORCING>
 FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &fz, int e) {
     const int mode = seg_mode(a.segs, e);
     if (mode == SEG_NONE) return;
@@ -222,47 +222,36 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
         const int nE = m.nE;
         const int c0 = m.coe0[e], c1 = m.coe1[e];
         const int n = m.nEoE[e];
-        const float qself = a.qe[e];
+        const float qself = a.fqu[e].y;
         float cor = 0.f, vt = 0.f;
         if (m.rows) {
-            // neighbours = the other edges of c0 then of c1, from the cells' rows:
-            // the row indices and weights are loaded before the dependent gathers
+            // neighbours = the other edges of c0 then of c1, from the cells' rows
             const int nC = m.nC;
             const unsigned short sl = m.eslot[e];
-            int k0 = 0;
+            int k = 0;
             for (int side = 0; side < 2; ++side) {
                 const int c = side ? c1 : c0;
                 const int nc = m.nEoC[c];
                 const int p = side ? (sl >> 8) : (sl & 0xff);
-                int xs[NMAX - 1];
-                float w[NMAX - 1];
-                FB_UNROLL
-                for (int j = 1; j < NMAX; ++j) {
-                    xs[j - 1] = e;
-                    w[j - 1] = 0.f;
-                    if (j < nc) {
-                        int jj = p + j;
-                        if (jj >= nc) jj -= nc;
-                        const int v = m.eocS[jj * nC + c];
-                        xs[j - 1] = v < 0 ? ~v : v;
-                        w[j - 1] = m.woeC32[(k0 + j - 1) * nE + e];
-                    }
+                for (int j = 1; j < nc; ++j) {
+                    int jj = p + j;
+                    if (jj >= nc) jj -= nc;
+                    const int v = m.eocS[jj * nC + c];
+                    const int x = v < 0 ? ~v : v;
+                    const float w = m.woeC32[k * nE + e];
+                    ++k;
+                    const float4 r = a.fqu[x];
+                    cor += w * r.x * (0.5f * (qself + r.y));
+                    if (FORCING) vt += w * r.z;
                 }
-                FB_UNROLL
-                for (int j = 0; j < NMAX - 1; ++j) {
-                    if (j < nc - 1) {
-                        cor += w[j] * a.Fe[xs[j]] * (0.5f * (qself + a.qe[xs[j]]));
-                        if (FORCING) vt += w[j] * a.u_in[xs[j]];
-                    }
-                }
-                k0 += nc - 1;
             }
         } else {
             for (int j = 0; j < n; ++j) {
                 const int x = m.eoe[j * nE + e];
                 const float w = m.woe32[j * nE + e];
-                cor += w * a.Fe[x] * (0.5f * (qself + a.qe[x]));
-                if (FORCING) vt += w * a.u_in[x];
+                const float4 r = a.fqu[x];
+                cor += w * r.x * (0.5f * (qself + r.y));
+                if (FORCING) vt += w * r.z;
             }
         }
         const float x0c = a.hst[c0], x1c = a.hst[c1];

@@ -70,10 +70,10 @@ __global__ void __launch_bounds__(TPB) eprep32_pass(DevMesh m, PrepArgs32 a) {
     if (e < a.hi) prep32_body(m, a, e);
 }
 
-template <bool FORCING, int NMAX>
+template <bool FORCING>
 __global__ void __launch_bounds__(TPB) edge32_pass(DevMesh m, EdgeArgs32 a, DevForcing fz) {
     const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < a.hi) edge32_body<FORCING, NMAX>(m, a, fz, e);
+    if (e < a.hi) edge32_body<FORCING>(m, a, fz, e);
 }
 
 
@@ -99,11 +99,16 @@ __global__ void __launch_bounds__(TPB) forcing32_pass(DevMesh m, DevForcing fz) 
 }
 
 // resting depth seen by the FP32 path: H per cell, mean over the present cells
-// of an edge, kite-weighted mean at a vertex
-__global__ void fp32_depths(DevMesh m, float *H32, float *He32, float *Hv32) {
+// of an edge (also in the per-edge record {l_e, d_e l_e / 4, H_e, 0}),
+// kite-weighted mean at a vertex
+__global__ void fp32_depths(DevMesh m, float *H32, float *He32, float *Hv32, float4 *estat) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < m.nC) H32[t] = (float)(-m.bottom[t]);
-    if (t < m.nE) He32[t] = (float)(-0.5 * (m.bottom[m.coe0[t]] + m.bottom[m.coe1[t]]));
+    if (t < m.nE) {
+        const float He = (float)(-0.5 * (m.bottom[m.coe0[t]] + m.bottom[m.coe1[t]]));
+        He32[t] = He;
+        estat[t] = make_float4(m.dv32[t], m.ke32[t], He, 0.f);
+    }
     if (t < m.nV) {
         double s = 0.0;
         for (int j = 0; j < 3; ++j) s += m.cKite[j * m.nV + t] * (-m.bottom[m.cov[j * m.nV + t]]);
@@ -215,16 +220,8 @@ static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &
             if (op.hi <= op.lo) return cudaSuccess;
             const EdgeArgs32 a = edge_args32(op, arr, g);
             const int nb = nblk(op.hi - op.lo);
-            if (m.maxE <= 6) {
-                if (fz.flags) edge32_pass<true, 6><<<nb, TPB, 0, st>>>(m, a, fz);
-                else edge32_pass<false, 6><<<nb, TPB, 0, st>>>(m, a, fz);
-            } else if (m.maxE <= 8) {
-                if (fz.flags) edge32_pass<true, 8><<<nb, TPB, 0, st>>>(m, a, fz);
-                else edge32_pass<false, 8><<<nb, TPB, 0, st>>>(m, a, fz);
-            } else {
-                if (fz.flags) edge32_pass<true, 12><<<nb, TPB, 0, st>>>(m, a, fz);
-                else edge32_pass<false, 12><<<nb, TPB, 0, st>>>(m, a, fz);
-            }
+            if (fz.flags) edge32_pass<true><<<nb, TPB, 0, st>>>(m, a, fz);
+            else edge32_pass<false><<<nb, TPB, 0, st>>>(m, a, fz);
         } break;
         case OP_SAVE:
         case OP_PRED:
@@ -245,9 +242,10 @@ static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &
     return cudaGetLastError();
 }
 
-cudaError_t launch_fp32_depths(const DevMesh &m, float *H32, float *He32, float *Hv32, cudaStream_t st) {
+cudaError_t launch_fp32_depths(const DevMesh &m, float *H32, float *He32, float *Hv32, float4 *estat,
+                               cudaStream_t st) {
     const int n = m.nE > m.nV ? (m.nE > m.nC ? m.nE : m.nC) : (m.nV > m.nC ? m.nV : m.nC);
-    fp32_depths<<<nblk(n), TPB, 0, st>>>(m, H32, He32, Hv32);
+    fp32_depths<<<nblk(n), TPB, 0, st>>>(m, H32, He32, Hv32, estat);
     return cudaGetLastError();
 }
 

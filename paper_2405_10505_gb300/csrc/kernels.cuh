@@ -26,6 +26,7 @@ struct DevMesh {
     // neighbour edges from the cells' edge rows: slots and weights in row order (FP32 path)
     const int *eocS;                    // edge rows with the sign n_{e,i} (~e for the second cell)
     const float *dv32, *ke32;           // l_e and d_e l_e / 4 per edge
+    const float4 *estat;                // per edge {l_e, d_e l_e / 4, H_e, 0} (H_e per state)
     const double *invA;                 // 1 / A_i
     int rows;                           // 1 when eslot / woeC32 are valid
     const unsigned short *eslot;
@@ -69,7 +70,8 @@ cudaError_t launch_op(const Op &op, const DevMesh &m, const DevArrays &arr, cons
 
 // FP32-tendency path: resting depths seen by the float kernels, and the
 // float shadows of the double time level (after any write of h, u)
-cudaError_t launch_fp32_depths(const DevMesh &m, float *H32, float *He32, float *Hv32, cudaStream_t st);
+cudaError_t launch_fp32_depths(const DevMesh &m, float *H32, float *He32, float *Hv32, float4 *estat,
+                               cudaStream_t st);
 cudaError_t launch_fp32_shadows(const DevMesh &m, const DevArrays &arr, cudaStream_t st);
 
 // caller-order <-> band-order copies

@@ -256,10 +256,11 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
                     const Seg &g = op.seg[k];
                     const double n = g.end - g.begin, slots = pc[g.end] - pc[g.begin];
                     if (fp32) {
-                        // nEoC, 1/A, K | signed edge row, u_in and l_e, d_e l_e/4 (an edge has 2 cells)
-                        b += n * (4 + 8 + 4) + slots * (4 + 2 + 2);
+                        // nEoC, 1/A, K | signed edge row, u_in and the 16-byte edge record
+                        // {l_e, d_e l_e/4, H_e} (an edge has 2 cells)
+                        b += n * (4 + 8 + 4) + slots * (4 + 2 + 8);
                         if (g.mode == SEG_KONLY) continue;
-                        b += n * (4 + 4) + slots * (4 + 2);          // xi_in, H | coc, l_e
+                        b += n * 4 + slots * 4;                      // xi_in | coc
                     } else {
                         // nEoC, K out | eoc, cKE, u_in (an edge is gathered by 2 cells)
                         b += n * (4 + 8) + slots * (4 + 8 + 4);
@@ -276,17 +277,18 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
             case OP_VERT:
                 b = (double)(op.hi - op.lo) * (3 * (4 + 4 + C + C) + C + (fp32 ? 4 : 0) + 1.5 * R + 0.5 * R + R);
                 break;
-            case OP_EPREP:
-                b = (double)(op.hi - op.lo) * (17 + (fp32 ? 4 : 0) + R + R * 2 * cpe + R * 2 * vpe + (fp32 ? 2 : 3) * R);
+            case OP_EPREP:   // fp32 writes the 16-byte record {F, q_e, u, 0}
+                b = (double)(op.hi - op.lo) * (17 + (fp32 ? 4 : 0) + R + R * 2 * cpe + R * 2 * vpe + (fp32 ? 16 : 3 * R));
                 break;
             case OP_EDGE:
                 for (int k = 0; k < op.nseg; ++k) {
                     const Seg &g = op.seg[k];
                     const double n = g.end - g.begin, slots = pe[g.end] - pe[g.begin];
-                    // ebnd, nEoE, Fe/qe, coe, invDc, K and hst at the cells (+ bottom in double);
-                    // neighbours: an index and a weight per slot, or (rows) the two cells' edge
-                    // rows, each row shared by the cell's edges, plus the two slots
-                    b += n * (1 + 4 + 2 * R + 8 + C + 2 * R * 2 * cpe + (fp32 ? 0 : 8 * 2 * cpe));
+                    // ebnd, nEoE, neighbour records (fp32: {F, q_e, u} 16 B; fp64: F, q_e, F q_e),
+                    // coe, invDc, K and hst at the cells (+ bottom in double); neighbours: an
+                    // index and a weight per slot, or (rows) the two cells' edge rows, each row
+                    // shared by the cell's edges, plus the two slots
+                    b += n * (1 + 4 + (fp32 ? 16 : 3 * R) + 8 + C + 2 * R * 2 * cpe + (fp32 ? 0 : 8 * 2 * cpe));
                     if (fp32 && hm.rows_canonical)
                         b += n * (2 + 2 * cpe * (4 + 4 * (pc[hm.nC] / hm.nC))) + slots * C;
                     else
@@ -295,7 +297,7 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
                     if (g.mode == SEG_INPLACE) b += n * (fp32 ? (8 + 8 + 4) : 16);
                     if (g.mode == SEG_ACC_SET) b += n * 8;
                     if (g.mode == SEG_ACC_ADD) b += n * 16;
-                    if (forcing) b += n * (R + 3 * R + (fp32 ? 4 : 0) + R * 2 * cpe);
+                    if (forcing) b += n * ((fp32 ? 0 : R) + 3 * R + (fp32 ? 4 : 0) + R * 2 * cpe);
                 }
                 break;
             case OP_SAVE: {
