@@ -271,7 +271,7 @@ def main():
     hbm, peak_src = peaks()
     achieved = dbytes / (dms / 1000.0) / 1e9
     kernel_name = {"cell": "cell_pass", "vertex": "vert_pass", "edge_prep": "eprep_pass",
-                   "edge": "edge_pass"}.get(dom, dom)
+                   "edge": "edge_pass", "trisk": "trisk_pass"}.get(dom, dom)
     traffic = traffic_for(args.workload, args.precision, kernel_name)
 
     # end to end through the public host-buffer call: H2D inputs, 1 step, D2H result

@@ -141,9 +141,12 @@ typedef struct fblts_mesh_info {
     int64_t cell_updates_per_step;
     /* IF-1 u IF-2 cells of each level pair */
     int64_t band_cells[8];
-    /* bit 0: the FP32 edge pass reads neighbour edges from the two cells'
-     * edge rows (every edgesOnEdge list is the other edges of the edge's two
-     * cells); otherwise it reads the edgesOnEdge lists */
+    /* bit 0: cell rows.  Every edgesOnEdge list is the other edges of the
+     * edge's two cells and weightsOnEdge is the kite-fraction TRiSK form
+     * n_{e,i} n_{e',i} (1/2 - sum of R_{i,v} from e to e') dvEdge[e'] /
+     * dcEdge[e] (R_{i,v} = kite / areaCell, matched to 1e-9), so the FP32
+     * path forms the TRiSK sums per cell from the cells' edge rows and kite
+     * fractions; otherwise it uses the edgesOnEdge / weightsOnEdge lists */
     int32_t flags;
 } fblts_mesh_info;
 fblts_status fblts_mesh_get_info(const fblts_mesh *mesh, fblts_mesh_info *info);
@@ -250,10 +253,14 @@ fblts_status fblts_state_launches_per_step(const fblts_state *state, int64_t *la
  * the launch count and alg_bytes[k] the algorithmic bytes: every array element
  * the launch's arithmetic must read or write, counted once at its storage
  * size (metadata included).  Arrays have FBLTS_PROFILE_KINDS entries; any may
- * be NULL.  Synchronises. */
+ * be NULL.  Synchronises.  FBLTS_PK_TRISK is the FP32 path's cell-side TRiSK
+ * pass, which replaces the edge prep on meshes whose neighbour lists and
+ * weights are the cells' edge rows and kite-fraction weights (mesh_info flags
+ * bit 0). */
 enum {
     FBLTS_PK_CELL = 0, FBLTS_PK_VERTEX, FBLTS_PK_EDGE_PREP, FBLTS_PK_EDGE, FBLTS_PK_SAVE,
-    FBLTS_PK_PREDICT, FBLTS_PK_CORRECT, FBLTS_PK_FORCING, FBLTS_PK_STEP_END, FBLTS_PROFILE_KINDS
+    FBLTS_PK_PREDICT, FBLTS_PK_CORRECT, FBLTS_PK_FORCING, FBLTS_PK_STEP_END, FBLTS_PK_TRISK,
+    FBLTS_PROFILE_KINDS
 };
 fblts_status fblts_state_profile_step(fblts_state *state, double *ms, int64_t *launches,
                                       double *alg_bytes);

@@ -65,7 +65,8 @@ SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts
            "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
            "fblts_state_time", "fblts_state_save", "fblts_state_load", "fblts_state_launches_per_step",
            "fblts_state_profile_step", "fblts_state_step_bytes", "fblts_diagnostics_static")
-PROFILE_KINDS = ("cell", "vertex", "edge_prep", "edge", "save", "predict", "correct", "forcing", "step_end")
+PROFILE_KINDS = ("cell", "vertex", "edge_prep", "edge", "save", "predict", "correct", "forcing", "step_end",
+                 "trisk")
 
 
 def library_path():

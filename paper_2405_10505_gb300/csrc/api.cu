@@ -176,7 +176,15 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     addd(hm.Av, &dm.Av);
     addf(slot_major(hm.cDiv, nC, mE), &dm.cDiv32);
     addf(slot_major(hm.cKE, nC, mE), &dm.cKE32);
-    addf(slot_major(hm.woe, nE, mE2), &dm.woe32);
+    {   // FP32 list weights W_{e,e'} / l_{e'}: the edge records carry l_{e'}
+        std::vector<double> w(hm.woe);
+        for (int e = 0; e < nE; ++e)
+            for (int j = 0; j < mE2; ++j) {
+                const double l = hm.dvE[hm.eoe[(size_t)e * mE2 + j]];
+                w[(size_t)e * mE2 + j] = l != 0.0 ? w[(size_t)e * mE2 + j] / l : 0.0;
+            }
+        addf(slot_major(w, nE, mE2), &dm.woe32);
+    }
     addf(hm.invDc, &dm.invDc32);
     addf(slot_major(hm.cVort, nV, 3), &dm.cVort32);
     addf(slot_major(hm.cKite, nV, 3), &dm.cKite32);
@@ -185,9 +193,12 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     addf(hm.dvE, &dm.dv32);
     addf(hm.keE, &dm.ke32);
     addd(hm.invA, &dm.invA);
-    dm.rows = hm.rows_canonical ? 1 : 0;
-    if (dm.rows) {
-        addf(slot_major(hm.woeC, nE, mE2), &dm.woeC32);
+    dm.rowS = hm.rows_canonical ? hm.rowS : 0;
+    if (dm.rowS) {
+        addi(hm.rowE, &dm.rowE);
+        addf(hm.rowP, &dm.rowP);
+        addi(hm.rowN, &dm.rowN);
+        addi(hm.rowV, &dm.rowV);
         std::vector<unsigned char> sl(hm.eslot.size() * 2);
         std::memcpy(sl.data(), hm.eslot.data(), sl.size());
         bkeep.push_back(std::move(sl));
@@ -358,7 +369,9 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         return !f32 || a == A_H || a == A_U || a == A_ACCH || a == A_ACCU || a == A_SH0 || a == A_SU0;
     };
     auto count = [&](int a) -> size_t {
-        if (a == A_FQU) return 4 * (size_t)nE;   // {F, q_e, u, 0} per edge (FP32 path)
+        // FP32 path: the edge records {l F, q_e, l u, 0}, or with cell rows the
+        // two cells' 16-byte shares per edge
+        if (a == A_FQU) return (m->dm.rowS ? 8 : 4) * (size_t)nE;
         return arr_is_cell(a) ? (size_t)nC : (arr_is_vert(a) ? (size_t)nV : (size_t)nE);
     };
     // every allocation in order; the sizing pass and the carving pass walk the same list
@@ -462,7 +475,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     fz.rho_air = p->rho_air > 0 ? p->rho_air : 1.225;
     for (int k = 0; k < 9; ++k) fz.vx[k] = p->vortex[k];
     fz.t0 = p->t0; fz.dt = p->dt; fz.step = s->d_step;
-    build_schedule(hm, p->dt, p->beta, s->sched);
+    build_schedule(hm, p->dt, p->beta, f32 && m->dm.rowS != 0, s->sched);
     schedule_bytes(hm, p->forcing, p->precision == FBLTS_FP32_TENDENCY, s->sched);
     if (cudaStreamSynchronize(s->st) != cudaSuccess) {
         set_error("state_init: %s", cudaGetErrorString(cudaGetLastError()));
@@ -597,15 +610,18 @@ extern "C" fblts_status fblts_state_load(fblts_state *s, const void *buf, size_t
     return FBLTS_OK;
 }
 
+// whether launch_op issues a kernel for this op
+static bool op_launches(const fblts_state *s, const Op &op) {
+    if (op.kind == OP_FORCING) return s->fz.flags != 0;
+    if (op.kind == OP_CELL || op.kind == OP_VERT || op.kind == OP_EPREP || op.kind == OP_EDGE || op.kind == OP_TRISK)
+        return op.hi > op.lo;
+    return true;
+}
+
 extern "C" fblts_status fblts_state_launches_per_step(const fblts_state *s, int64_t *launches) {
     if (!s || !launches) { set_error("launches_per_step: NULL argument"); return FBLTS_E_ARG; }
     int64_t n = 0;
-    for (const Op &op : s->sched.ops) {
-        if (op.kind == OP_FORCING && !s->fz.flags) continue;
-        if ((op.kind == OP_CELL || op.kind == OP_VERT || op.kind == OP_EPREP || op.kind == OP_EDGE) && op.hi <= op.lo)
-            continue;
-        n++;
-    }
+    for (const Op &op : s->sched.ops) n += op_launches(s, op) ? 1 : 0;
     *launches = n;
     return FBLTS_OK;
 }
@@ -620,6 +636,7 @@ static int op_kind_profile(int kind) {
         case OP_PRED: return FBLTS_PK_PREDICT;
         case OP_FINAL: return FBLTS_PK_CORRECT;
         case OP_FORCING: return FBLTS_PK_FORCING;
+        case OP_TRISK: return FBLTS_PK_TRISK;
         default: return FBLTS_PK_STEP_END;
     }
 }
@@ -648,10 +665,7 @@ extern "C" fblts_status fblts_state_profile_step(fblts_state *s, double *ms, int
     int64_t tl[FBLTS_PROFILE_KINDS] = {0};
     for (size_t i = 0; i < n && st == FBLTS_OK; ++i) {
         const Op &op = s->sched.ops[i];
-        bool empty = (op.kind == OP_FORCING && !s->fz.flags) ||
-                     ((op.kind == OP_CELL || op.kind == OP_VERT || op.kind == OP_EPREP || op.kind == OP_EDGE) &&
-                      op.hi <= op.lo);
-        if (empty) continue;
+        if (!op_launches(s, op)) continue;
         float t = 0.f;
         cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
         int k = op_kind_profile(op.kind);

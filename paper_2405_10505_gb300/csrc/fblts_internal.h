@@ -53,12 +53,21 @@ struct HostMesh {
     std::vector<double> cDiv, cKE;         // [nC*maxE]
     std::vector<double> cVort, cKite;      // [nV*3]
     std::vector<double> woe;               // [nE*maxE2]
-    // Neighbour edges read from the two cells' edge rows: slot of the edge in
-    // the row of c0 (low byte) and c1 (high byte), and the weights reordered to
-    // [row of c0 from slot+1 cyclically, row of c1 from slot+1 cyclically].
+    // Neighbour edges read from the two cells' edge rows (FP32 edge pass).
+    // Valid when every edge's neighbours are exactly the other edges of its two
+    // cells and the weights are the kite-fraction TRiSK weights: then rowE holds
+    // each cell's signed edge row and rowP the prefix sums of its kite
+    // fractions, padded to rowS (8 or 12) slots, and eslot packs, in 4-bit
+    // fields, the edge's slot in the row of c0 and of c1 and the two row lengths.
+    // rowN holds the neighbour cell across each slot's edge (the cell itself on
+    // a no-flow edge) and rowV the vertex at the counter-clockwise end of the
+    // slot's edge, for the cell-side TRiSK pass.
     bool rows_canonical = false;
+    int rowS = 8;
+    std::vector<int> rowE;                 // [nC*rowS]
+    std::vector<double> rowP;              // [nC*rowS]
+    std::vector<int> rowN, rowV;           // [nC*rowS]
     std::vector<uint16_t> eslot;           // [nE]
-    std::vector<double> woeC;              // [nE*maxE2]
     std::vector<double> invDc, area, fV, Av;
     std::vector<double> cosE, sinE, xC, yC, xE, yE;
     bool has_angle = false, has_xy_cell = false, has_xy_edge = false;
@@ -104,7 +113,7 @@ struct Seg {
 constexpr int MAX_SEG = 6;
 
 enum OpKind : int {
-    OP_CELL = 0, OP_VERT, OP_EPREP, OP_EDGE, OP_SAVE, OP_PRED, OP_FINAL, OP_FORCING, OP_STEP_END
+    OP_CELL = 0, OP_VERT, OP_EPREP, OP_EDGE, OP_SAVE, OP_PRED, OP_FINAL, OP_FORCING, OP_STEP_END, OP_TRISK
 };
 
 struct Op {
@@ -133,7 +142,10 @@ struct Schedule {
     int64_t launches = 0;
 };
 
-void build_schedule(const HostMesh &hm, double dt, const double beta[3], Schedule &s);
+// trisk_cells: the Coriolis / tangential sums are formed per cell (OP_TRISK
+// over the cells of the edge pass) instead of per edge from edge records
+// (OP_EPREP over the edges and their neighbours)
+void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, Schedule &s);
 // fills Op::alg_bytes of every op (forcing: the edge passes read the forcing fields)
 void schedule_bytes(const HostMesh &hm, int forcing_flags, bool fp32, Schedule &s);
 

@@ -30,11 +30,22 @@ struct PrepArgs32 {
     float4 *fqu;      // per edge {F_e, q_e, u_e, 0}
 };
 
+// Cell-side TRiSK pass: per slot of each cell, the share {t, s_v, B_i, xi*_i}
+// of the cell in its edge's Coriolis and tangential sums (see trisk32_body),
+// written to half[2 e + side] (side 0 = first cell of e).
+struct TriskArgs32 {
+    int lo, hi;
+    const float *u_in, *hst, *K, *q;
+    float4 *half;
+    float g, inv_rho0;
+};
+
 struct EdgeArgs32 {
     SegSet segs;
     int lo, hi;
     const float *u_in, *hst, *K, *u0;
     const float4 *fqu;
+    const float4 *half;
     float *us_out, *u_shadow;
     double *u_state, *acc;
     double cdt;
@@ -79,11 +90,17 @@ inline PrepArgs32 prep_args32(const Op &op, const DevArrays &arr) {
     return PrepArgs32{op.lo, op.hi, f_in(arr, op.in_u), arr.f[op.hst], arr.f[A_Q], (float4 *)arr.f[A_FQU]};
 }
 
+inline TriskArgs32 trisk_args32(const Op &op, const DevArrays &arr, double g, double rho0) {
+    return TriskArgs32{op.lo, op.hi, f_in(arr, op.in_u), arr.f[op.hst], arr.f[A_K], arr.f[A_Q],
+                       (float4 *)arr.f[A_FQU], (float)g, (float)(rho0 > 0.0 ? 1.0 / rho0 : 0.0)};
+}
+
 inline EdgeArgs32 edge_args32(const Op &op, const DevArrays &arr, double g) {
     EdgeArgs32 a;
     a.segs = segs_of(op);
     a.lo = op.lo; a.hi = op.hi;
     a.u_in = f_in(arr, op.in_u); a.hst = arr.f[op.hst]; a.K = arr.f[A_K]; a.fqu = (const float4 *)arr.f[A_FQU];
+    a.half = (const float4 *)arr.f[A_FQU];
     a.u0 = f_in(arr, op.u0); a.us_out = arr.f[op.out_u]; a.u_shadow = arr.u32;
     a.u_state = arr.a[A_U]; a.acc = arr.a[A_ACCU];
     a.cdt = op.cdt; a.g = (float)g;
@@ -201,51 +218,119 @@ FB_HD void vert32_body(const DevMesh &m, const VertArgs32 &a, int v) {
     a.q[v] = (z + m.fV32[v]) / (m.Hv32[v] + xv);
 }
 
-// Edge e: {F_e = (H_e + (xi_c0 + xi_c1)/2) u_e, q_e, u_e} as one 16-byte
-// record, so the edge pass gathers a neighbour with one load.
+// Edge e: {l_e F_e, q_e, l_e u_e, 0} with F_e = (H_e + (xi_c0 + xi_c1)/2) u_e,
+// one 16-byte record, so the edge pass gathers a neighbour with one load.
+// The neighbour's l_{e'} of the TRiSK weight travels with its record.
 FB_HD void prep32_body(const DevMesh &m, const PrepArgs32 &a, int e) {
     const int c0 = m.coe0[e], c1 = m.coe1[e];
     const float ue = a.u_in[e];
-    const float F = m.ebnd[e] ? 0.f : (m.He32[e] + 0.5f * (a.hst[c0] + a.hst[c1])) * ue;
-    a.fqu[e] = make_float4(F, 0.5f * (a.q[m.voe0[e]] + a.q[m.voe1[e]]), ue, 0.f);
+    const float lu = m.dv32[e] * ue;   // l_e = 0 on no-flow edges
+    const float lF = (m.He32[e] + 0.5f * (a.hst[c0] + a.hst[c1])) * lu;
+    a.fqu[e] = make_float4(lF, 0.5f * (a.q[m.voe0[e]] + a.q[m.voe1[e]]), lu, 0.f);
+}
+
+// Cell i's share in the momentum tendency of each of its edges (Sec. 2.3,
+// Eq. trisk_vorticity with the TRiSK flux mapping, and the gradient of
+// Eq. nonlinear_swe).  For edges e_k, e_j of the cell (slots k, j; signs
+// n_k, n_j; kite-fraction prefix P) the weight is
+//   W_kj d_{e_k} = n_k n_j (1/2 - (P_j - P_k + [j < k])) l_{e_j},
+// and with y_j = n_j X_j the sum over j != k reduces to
+//   sum_j W_kj d X_j / l_j = n_k (1/2 (T - y_k) - T_P + P_k T - C_k),
+// T = sum_j y_j, T_P = sum_j P_j y_j, C_k = sum_{j<k} y_j: O(n) per cell.
+// X = l F (F = h_e u from the FB-averaged thickness) gives s0, X = l F q_e
+// gives s1, X = l u gives s_v.  The share of slot k is
+//   {t = q_{e_k} s0 + s1, s_v, B_i = K_i + g xi*_i (+ p_s / rho0), xi*_i},
+// so the edge pass forms Phi_e = [(t_0 + t_1)/2 - (B_c1 - B_c0)] / d_e from
+// two coalesced loads.  q_{e_k} = (q at the two vertices of e_k) / 2: the
+// row's vertex k is the counter-clockwise end of e_k, vertex k-1 the other.
+// Rows are padded to S slots with valid indices; slots >= nEoC are masked.
+template <int S, bool VORTEX>
+FB_HD void trisk32_body(const DevMesh &m, const TriskArgs32 &a, const DevForcing &fz, int i) {
+    const int n = m.nEoC[i];
+    int re[S], rn[S], rv[S];
+    float P[S];
+    {
+        const int4 *e4 = reinterpret_cast<const int4 *>(m.rowE + (size_t)i * S);
+        const int4 *n4 = reinterpret_cast<const int4 *>(m.rowN + (size_t)i * S);
+        const int4 *v4 = reinterpret_cast<const int4 *>(m.rowV + (size_t)i * S);
+        const float4 *p4 = reinterpret_cast<const float4 *>(m.rowP + (size_t)i * S);
+        FB_UNROLL
+        for (int q = 0; q < S / 4; ++q) {
+            const int4 te = e4[q], tn = n4[q], tv = v4[q];
+            const float4 tp = p4[q];
+            re[4 * q] = te.x; re[4 * q + 1] = te.y; re[4 * q + 2] = te.z; re[4 * q + 3] = te.w;
+            rn[4 * q] = tn.x; rn[4 * q + 1] = tn.y; rn[4 * q + 2] = tn.z; rn[4 * q + 3] = tn.w;
+            rv[4 * q] = tv.x; rv[4 * q + 1] = tv.y; rv[4 * q + 2] = tv.z; rv[4 * q + 3] = tv.w;
+            P[4 * q] = tp.x; P[4 * q + 1] = tp.y; P[4 * q + 2] = tp.z; P[4 * q + 3] = tp.w;
+        }
+    }
+    const float xs = a.hst[i];
+    float B = a.K[i] + a.g * xs;
+    if (VORTEX) B += fz.ps32[i] * a.inv_rho0;
+    float lF[S], lu[S], qv[S];
+    FB_UNROLL
+    for (int j = 0; j < S; ++j) {
+        const int e = re[j] < 0 ? ~re[j] : re[j];
+        const float4 st = m.estat[e];
+        const float u = a.u_in[e];
+        const float xn = a.hst[rn[j]];
+        qv[j] = a.q[rv[j]];
+        lu[j] = j < n ? st.x * u : 0.f;
+        lF[j] = (st.z + 0.5f * (xs + xn)) * lu[j];
+    }
+    float qlast = qv[0];
+    FB_UNROLL
+    for (int j = 1; j < S; ++j) qlast = (j == n - 1) ? qv[j] : qlast;
+    float qe[S];
+    float T0 = 0.f, T1 = 0.f, Tv = 0.f, P0 = 0.f, P1 = 0.f, Pv = 0.f;
+    FB_UNROLL
+    for (int j = 0; j < S; ++j) {
+        qe[j] = 0.5f * ((j == 0 ? qlast : qv[j - 1]) + qv[j]);
+        const float sg = re[j] < 0 ? -1.f : 1.f;
+        const float y0 = sg * lF[j], y1 = y0 * qe[j], yv = sg * lu[j];
+        T0 += y0; T1 += y1; Tv += yv;
+        P0 += P[j] * y0; P1 += P[j] * y1; Pv += P[j] * yv;
+    }
+    float C0 = 0.f, C1 = 0.f, Cv = 0.f;
+    FB_UNROLL
+    for (int k = 0; k < S; ++k) {
+        const float sg = re[k] < 0 ? -1.f : 1.f;
+        const float y0 = sg * lF[k], y1 = y0 * qe[k], yv = sg * lu[k];
+        if (k < n) {
+            const float s0 = sg * (0.5f * (T0 - y0) - P0 + P[k] * T0 - C0);
+            const float s1 = sg * (0.5f * (T1 - y1) - P1 + P[k] * T1 - C1);
+            const float sv = sg * (0.5f * (Tv - yv) - Pv + P[k] * Tv - Cv);
+            const int e = re[k] < 0 ? ~re[k] : re[k];
+            a.half[2 * e + (re[k] < 0 ? 1 : 0)] = make_float4(qe[k] * s0 + s1, sv, B, xs);
+        }
+        C0 += y0; C1 += y1; Cv += yv;
+    }
 }
 
 // Edge e: Phi_e in float (the pressure gradient g (xi_c1 - xi_c0) / d_e needs
 // no cancellation of large depths), stage value u_s = u0 + c tau Phi, in
-// place u += c tau Phi in double, or the correction sum in double.
-template <bool FORCING>
+// place u += c tau Phi in double, or the correction sum in double.  SHARES:
+// from the two cells' shares of the cell-side TRiSK pass; else from the edge
+// records over explicit neighbour lists.
+template <bool SHARES, bool FORCING>
 FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &fz, int e) {
     const int mode = seg_mode(a.segs, e);
     if (mode == SEG_NONE) return;
     float phi = 0.f;
     if (!m.ebnd[e]) {
-        const int nE = m.nE;
-        const int c0 = m.coe0[e], c1 = m.coe1[e];
-        const int n = m.nEoE[e];
-        const float qself = a.fqu[e].y;
-        float cor = 0.f, vt = 0.f;
-        if (m.rows) {
-            // neighbours = the other edges of c0 then of c1, from the cells' rows
-            const int nC = m.nC;
-            const unsigned short sl = m.eslot[e];
-            int k = 0;
-            for (int side = 0; side < 2; ++side) {
-                const int c = side ? c1 : c0;
-                const int nc = m.nEoC[c];
-                const int p = side ? (sl >> 8) : (sl & 0xff);
-                for (int j = 1; j < nc; ++j) {
-                    int jj = p + j;
-                    if (jj >= nc) jj -= nc;
-                    const int v = m.eocS[jj * nC + c];
-                    const int x = v < 0 ? ~v : v;
-                    const float w = m.woeC32[k * nE + e];
-                    ++k;
-                    const float4 r = a.fqu[x];
-                    cor += w * r.x * (0.5f * (qself + r.y));
-                    if (FORCING) vt += w * r.z;
-                }
-            }
+        const float idc = m.invDc32[e];
+        float vt = 0.f, xsum = 0.f;
+        if constexpr (SHARES) {
+            const float4 h0 = a.half[2 * e], h1 = a.half[2 * e + 1];
+            phi = idc * (0.5f * (h0.x + h1.x) - (h1.z - h0.z));
+            vt = idc * (h0.y + h1.y);
+            xsum = h0.w + h1.w;
         } else {
+            // explicit neighbour list; the weights are W_{e,e'} / l_{e'}
+            const int nE = m.nE, n = m.nEoE[e];
+            const int c0 = m.coe0[e], c1 = m.coe1[e];
+            const float qself = a.fqu[e].y;
+            float cor = 0.f;
             for (int j = 0; j < n; ++j) {
                 const int x = m.eoe[j * nE + e];
                 const float w = m.woe32[j * nE + e];
@@ -253,20 +338,20 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
                 cor += w * r.x * (0.5f * (qself + r.y));
                 if (FORCING) vt += w * r.z;
             }
+            const float x0c = a.hst[c0], x1c = a.hst[c1];
+            const float grad = (a.K[c1] - a.K[c0]) + a.g * (x1c - x0c);
+            phi = cor - grad * idc;
+            xsum = x0c + x1c;
+            if (FORCING && (fz.flags & FBLTS_FORCE_VORTEX)) phi -= (fz.ps32[c1] - fz.ps32[c0]) * idc / (float)fz.rho0;
         }
-        const float x0c = a.hst[c0], x1c = a.hst[c1];
-        const float grad = (a.K[c1] - a.K[c0]) + a.g * (x1c - x0c);
-        phi = cor - grad * m.invDc32[e];
         if (FORCING) {
             const float ue = a.u_in[e];
-            const float he = m.He32[e] + 0.5f * (x0c + x1c);
+            const float he = m.He32[e] + 0.5f * xsum;
             if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
                 const float dn = fz.windN32[e] - ue, dt = fz.windT32[e] - vt;
                 phi += fz.cw32[e] * sqrtf(dn * dn + dt * dt) * dn / he;
             }
             if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue / he;
-            if (fz.flags & FBLTS_FORCE_VORTEX)
-                phi -= (fz.ps32[c1] - fz.ps32[c0]) * m.invDc32[e] / (float)fz.rho0;
         }
     }
     switch (mode) {

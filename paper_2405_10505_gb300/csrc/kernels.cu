@@ -4,6 +4,8 @@
 // each index (stage update, in-place update, correction sum, kinetic energy
 // only) comes from the launch's segment list.  The passes use no atomics, so
 // every result is bit-reproducible run to run.
+#include <utility>
+
 #include "kernel_bodies32.cuh"
 
 namespace fblts {
@@ -12,43 +14,60 @@ namespace {
 
 constexpr int TPB = 256;
 
+// Programmatic dependent launch: a kernel of the schedule may be scheduled
+// while its predecessor drains; it waits here, before touching memory, until
+// the predecessor's results are visible.
+__device__ __forceinline__ void wait_predecessor() {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
+    cudaGridDependencySynchronize();
+#endif
+}
+
 __global__ void __launch_bounds__(TPB) cell_pass(DevMesh m, CellArgs a) {
+    wait_predecessor();
     const int i = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.hi) cell_body(m, a, i);
 }
 
 __global__ void __launch_bounds__(TPB) vert_pass(DevMesh m, VertArgs a) {
+    wait_predecessor();
     const int v = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (v < a.hi) vert_body(m, a, v);
 }
 
 __global__ void __launch_bounds__(TPB) eprep_pass(DevMesh m, PrepArgs a) {
+    wait_predecessor();
     const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (e < a.hi) prep_body(m, a, e);
 }
 
 template <bool FORCING>
 __global__ void __launch_bounds__(TPB) edge_pass(DevMesh m, EdgeArgs a, DevForcing fz) {
+    wait_predecessor();
     const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (e < a.hi) edge_body<FORCING>(m, a, fz, e);
 }
 
 __global__ void __launch_bounds__(TPB) save_pass(IfArgs a) {
+    wait_predecessor();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < a.n) save_body(a, t);
 }
 
 __global__ void __launch_bounds__(TPB) pred_pass(IfArgs a) {
+    wait_predecessor();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < a.n) pred_body(a, t);
 }
 
 __global__ void __launch_bounds__(TPB) final_pass(IfArgs a, const unsigned char *ebnd) {
+    wait_predecessor();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < a.n) final_body(a, ebnd, t);
 }
 
 __global__ void __launch_bounds__(TPB) forcing_pass(DevMesh m, DevForcing fz) {
+    wait_predecessor();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const double time = fz.t0 + (double)(*fz.step) * fz.dt;
     forcing_body(m, fz, time, t);
@@ -56,43 +75,58 @@ __global__ void __launch_bounds__(TPB) forcing_pass(DevMesh m, DevForcing fz) {
 
 template <int NMAX>
 __global__ void __launch_bounds__(TPB) cell32_pass(DevMesh m, CellArgs32 a) {
+    wait_predecessor();
     const int i = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.hi) cell32_body<NMAX>(m, a, i);
 }
 
 __global__ void __launch_bounds__(TPB) vert32_pass(DevMesh m, VertArgs32 a) {
+    wait_predecessor();
     const int v = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (v < a.hi) vert32_body(m, a, v);
 }
 
 __global__ void __launch_bounds__(TPB) eprep32_pass(DevMesh m, PrepArgs32 a) {
+    wait_predecessor();
     const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (e < a.hi) prep32_body(m, a, e);
 }
 
-template <bool FORCING>
+template <bool SHARES, bool FORCING>
 __global__ void __launch_bounds__(TPB) edge32_pass(DevMesh m, EdgeArgs32 a, DevForcing fz) {
+    wait_predecessor();
     const int e = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < a.hi) edge32_body<FORCING>(m, a, fz, e);
+    if (e < a.hi) edge32_body<SHARES, FORCING>(m, a, fz, e);
+}
+
+template <int S, bool VORTEX>
+__global__ void __launch_bounds__(TPB) trisk32_pass(DevMesh m, TriskArgs32 a, DevForcing fz) {
+    wait_predecessor();
+    const int i = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.hi) trisk32_body<S, VORTEX>(m, a, fz, i);
 }
 
 
 __global__ void __launch_bounds__(TPB) save32_pass(IfArgs32 a) {
+    wait_predecessor();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < a.n) save32_body(a, t);
 }
 
 __global__ void __launch_bounds__(TPB) pred32_pass(IfArgs32 a) {
+    wait_predecessor();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < a.n) pred32_body(a, t);
 }
 
 __global__ void __launch_bounds__(TPB) final32_pass(IfArgs32 a, const unsigned char *ebnd) {
+    wait_predecessor();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < a.n) final32_body(a, ebnd, t);
 }
 
 __global__ void __launch_bounds__(TPB) forcing32_pass(DevMesh m, DevForcing fz) {
+    wait_predecessor();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const double time = fz.t0 + (double)(*fz.step) * fz.dt;
     forcing32_body(m, fz, time, t);
@@ -123,7 +157,10 @@ __global__ void fp32_shadows(const double *h, const double *b, const double *u, 
     if (t < nE) u32[t] = (float)u[t];
 }
 
-__global__ void step_end(long long *step) { *step += 1; }
+__global__ void step_end(long long *step) {
+    wait_predecessor();
+    *step += 1;
+}
 
 __global__ void gather_kernel(double *dst, const double *src, const int *idx, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -196,7 +233,29 @@ __global__ void check_kernel(const double *h, int nC, const double *u, int nE, i
 
 inline int nblk(long long n) { return (int)((n + TPB - 1) / TPB); }
 
+// launch with the programmatic-stream-serialisation attribute (see wait_predecessor)
+template <typename... KArgs, typename... Args>
+cudaError_t pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 }  // namespace
+
+#define CK_L(x)                                  \
+    do {                                         \
+        cudaError_t e__ = (x);                   \
+        if (e__ != cudaSuccess) return e__;      \
+    } while (0)
 
 static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &arr, const DevForcing &fz,
                                double g, long long *step_counter, cudaStream_t st) {
@@ -204,37 +263,57 @@ static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &
         case OP_CELL: {
             if (op.hi <= op.lo) return cudaSuccess;
             const CellArgs32 a = cell_args32(op, arr, m);
-            if (m.maxE <= 6) cell32_pass<6><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, a);
-            else if (m.maxE <= 8) cell32_pass<8><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, a);
-            else cell32_pass<12><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, a);
+            if (m.maxE <= 6) CK_L(pdl(cell32_pass<6>, nblk(op.hi - op.lo), TPB, st, m, a));
+            else if (m.maxE <= 8) CK_L(pdl(cell32_pass<8>, nblk(op.hi - op.lo), TPB, st, m, a));
+            else CK_L(pdl(cell32_pass<12>, nblk(op.hi - op.lo), TPB, st, m, a));
         } break;
         case OP_VERT:
             if (op.hi <= op.lo) return cudaSuccess;
-            vert32_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, vert_args32(op, arr));
+            CK_L(pdl(vert32_pass, nblk(op.hi - op.lo), TPB, st, m, vert_args32(op, arr)));
             break;
         case OP_EPREP:
             if (op.hi <= op.lo) return cudaSuccess;
-            eprep32_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, prep_args32(op, arr));
+            CK_L(pdl(eprep32_pass, nblk(op.hi - op.lo), TPB, st, m, prep_args32(op, arr)));
             break;
         case OP_EDGE: {
             if (op.hi <= op.lo) return cudaSuccess;
             const EdgeArgs32 a = edge_args32(op, arr, g);
             const int nb = nblk(op.hi - op.lo);
-            if (fz.flags) edge32_pass<true><<<nb, TPB, 0, st>>>(m, a, fz);
-            else edge32_pass<false><<<nb, TPB, 0, st>>>(m, a, fz);
+            if (m.rowS) {
+                if (fz.flags) CK_L(pdl(edge32_pass<true, true>, nb, TPB, st, m, a, fz));
+                else CK_L(pdl(edge32_pass<true, false>, nb, TPB, st, m, a, fz));
+            } else {
+                if (fz.flags) CK_L(pdl(edge32_pass<false, true>, nb, TPB, st, m, a, fz));
+                else CK_L(pdl(edge32_pass<false, false>, nb, TPB, st, m, a, fz));
+            }
+        } break;
+        case OP_TRISK: {
+            if (op.hi <= op.lo) return cudaSuccess;
+            const TriskArgs32 a = trisk_args32(op, arr, g, fz.rho0);
+            const int nb = nblk(op.hi - op.lo);
+            const bool vx = (fz.flags & FBLTS_FORCE_VORTEX) != 0;
+            if (m.rowS == 8) {
+                if (vx) CK_L(pdl(trisk32_pass<8, true>, nb, TPB, st, m, a, fz));
+                else CK_L(pdl(trisk32_pass<8, false>, nb, TPB, st, m, a, fz));
+            } else if (m.rowS == 12) {
+                if (vx) CK_L(pdl(trisk32_pass<12, true>, nb, TPB, st, m, a, fz));
+                else CK_L(pdl(trisk32_pass<12, false>, nb, TPB, st, m, a, fz));
+            } else {
+                return cudaErrorInvalidValue;   // the schedule emits OP_TRISK only with cell rows
+            }
         } break;
         case OP_SAVE:
         case OP_PRED:
         case OP_FINAL: {
             IfArgs32 a = if_args32(op, arr, m);
             if (a.n <= 0) return cudaSuccess;
-            if (op.kind == OP_SAVE) save32_pass<<<nblk(a.n), TPB, 0, st>>>(a);
-            else if (op.kind == OP_PRED) pred32_pass<<<nblk(a.n), TPB, 0, st>>>(a);
-            else final32_pass<<<nblk(a.n), TPB, 0, st>>>(a, m.ebnd);
+            if (op.kind == OP_SAVE) CK_L(pdl(save32_pass, nblk(a.n), TPB, st, a));
+            else if (op.kind == OP_PRED) CK_L(pdl(pred32_pass, nblk(a.n), TPB, st, a));
+            else CK_L(pdl(final32_pass, nblk(a.n), TPB, st, a, m.ebnd));
         } break;
         case OP_FORCING:
             if (!fz.flags) return cudaSuccess;
-            forcing32_pass<<<nblk(m.nE > m.nC ? m.nE : m.nC), TPB, 0, st>>>(m, fz);
+            CK_L(pdl(forcing32_pass, nblk(m.nE > m.nC ? m.nE : m.nC), TPB, st, m, fz));
             break;
         case OP_STEP_END: step_end<<<1, 1, 0, st>>>(step_counter); break;
         default: return cudaErrorInvalidValue;
@@ -261,33 +340,33 @@ cudaError_t launch_op(const Op &op, const DevMesh &m, const DevArrays &arr, cons
     switch (op.kind) {
         case OP_CELL:
             if (op.hi <= op.lo) return cudaSuccess;
-            cell_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, cell_args(op, arr));
+            CK_L(pdl(cell_pass, nblk(op.hi - op.lo), TPB, st, m, cell_args(op, arr)));
             break;
         case OP_VERT:
             if (op.hi <= op.lo) return cudaSuccess;
-            vert_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, vert_args(op, arr));
+            CK_L(pdl(vert_pass, nblk(op.hi - op.lo), TPB, st, m, vert_args(op, arr)));
             break;
         case OP_EPREP:
             if (op.hi <= op.lo) return cudaSuccess;
-            eprep_pass<<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, prep_args(op, arr));
+            CK_L(pdl(eprep_pass, nblk(op.hi - op.lo), TPB, st, m, prep_args(op, arr)));
             break;
         case OP_EDGE:
             if (op.hi <= op.lo) return cudaSuccess;
-            if (fz.flags) edge_pass<true><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, edge_args(op, arr, g), fz);
-            else edge_pass<false><<<nblk(op.hi - op.lo), TPB, 0, st>>>(m, edge_args(op, arr, g), fz);
+            if (fz.flags) CK_L(pdl(edge_pass<true>, nblk(op.hi - op.lo), TPB, st, m, edge_args(op, arr, g), fz));
+            else CK_L(pdl(edge_pass<false>, nblk(op.hi - op.lo), TPB, st, m, edge_args(op, arr, g), fz));
             break;
         case OP_SAVE:
         case OP_PRED:
         case OP_FINAL: {
             IfArgs a = if_args(op, arr);
             if (a.n <= 0) return cudaSuccess;
-            if (op.kind == OP_SAVE) save_pass<<<nblk(a.n), TPB, 0, st>>>(a);
-            else if (op.kind == OP_PRED) pred_pass<<<nblk(a.n), TPB, 0, st>>>(a);
-            else final_pass<<<nblk(a.n), TPB, 0, st>>>(a, m.ebnd);
+            if (op.kind == OP_SAVE) CK_L(pdl(save_pass, nblk(a.n), TPB, st, a));
+            else if (op.kind == OP_PRED) CK_L(pdl(pred_pass, nblk(a.n), TPB, st, a));
+            else CK_L(pdl(final_pass, nblk(a.n), TPB, st, a, m.ebnd));
         } break;
         case OP_FORCING:
             if (!fz.flags) return cudaSuccess;
-            forcing_pass<<<nblk(m.nE > m.nC ? m.nE : m.nC), TPB, 0, st>>>(m, fz);
+            CK_L(pdl(forcing_pass, nblk(m.nE > m.nC ? m.nE : m.nC), TPB, st, m, fz));
             break;
         case OP_STEP_END: step_end<<<1, 1, 0, st>>>(step_counter); break;
         default: return cudaErrorInvalidValue;

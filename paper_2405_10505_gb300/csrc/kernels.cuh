@@ -28,9 +28,13 @@ struct DevMesh {
     const float *dv32, *ke32;           // l_e and d_e l_e / 4 per edge
     const float4 *estat;                // per edge {l_e, d_e l_e / 4, H_e, 0} (H_e per state)
     const double *invA;                 // 1 / A_i
-    int rows;                           // 1 when eslot / woeC32 are valid
-    const unsigned short *eslot;
-    const float *woeC32;
+    // neighbour edges from the cells' edge rows (FP32 edge pass): rowS = 8 or
+    // 12 when valid, else 0 (explicit lists eoe / woe32, woe32 = W / l_{e'})
+    int rowS;
+    const unsigned short *eslot;        // slot in the row of c0 | of c1 << 4 | row lengths << 8, << 12
+    const int *rowE;                    // [nC * rowS] signed edge rows, padded
+    const float *rowP;                  // [nC * rowS] prefix sums of the kite fractions
+    const int *rowN, *rowV;             // [nC * rowS] neighbour cell / counter-clockwise vertex per slot
     // resting depth H = -b as seen by the FP32 path: per cell, edge mean, vertex mean (per state)
     const float *H32, *He32, *Hv32;
 };

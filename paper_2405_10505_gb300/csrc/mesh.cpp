@@ -475,32 +475,76 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
         hm.dvE[e] = d->dvEdge[eo];
         hm.keE[e] = 0.25 * d->dcEdge[eo] * d->dvEdge[eo];
     }
-    // neighbour edges as the two cells' edge rows (see HostMesh::rows_canonical)
+    // Neighbour edges of the FP32 edge pass from the two cells' edge rows, with
+    // the weights re-derived from kite fractions (see HostMesh::rows_canonical).
+    // R[i][k] = kite of cell i at the counter-clockwise end of its edge slot k / A_i;
+    // P[i][k] = sum_{s<k} R[i][s].  For e at slot p and e' at slot j of cell i,
+    // the kite sum from e counter-clockwise up to e' is P[j] - P[p] (+1 when j < p),
+    // and W_{e,e'} = n_{e,i} n_{e',i} (1/2 - that sum) l_{e'} / d_e.
+    hm.rowS = W <= 8 ? 8 : 12;
+    hm.rows_canonical = W <= 12;
+    hm.rowE.assign((size_t)nC * hm.rowS, 0);
+    hm.rowP.assign((size_t)nC * hm.rowS, 0.0);
+    hm.rowN.assign((size_t)nC * hm.rowS, 0);
+    hm.rowV.assign((size_t)nC * hm.rowS, 0);
+    for (int i = 0; i < nC && hm.rows_canonical; ++i) {
+        const int io = hm.cell_n2o[i], n = hm.nEoC[i];
+        double P = 0.0;
+        for (int k = 0; k < hm.rowS; ++k) {
+            const size_t r = (size_t)i * hm.rowS + k;
+            hm.rowE[r] = k < n ? hm.eocS[(size_t)i * W + k] : hm.eoc[(size_t)i * W];
+            hm.rowP[r] = k < n ? P : 0.0;
+            hm.rowN[r] = k < n ? hm.coc[(size_t)i * W + k] : i;
+            hm.rowV[r] = hm.rowV[(size_t)i * hm.rowS];
+            if (k >= n) continue;
+            const int eo = hm.edge_n2o[hm.eoc[(size_t)i * W + k]];
+            const int vend = coe[2 * eo] == io ? voe[2 * eo + 1] : voe[2 * eo];
+            hm.rowV[r] = vend >= 0 ? v2n[vend] : 0;
+            double kite = 0.0;
+            bool found = false;
+            if (vend >= 0)
+                for (int j = 0; j < 3; ++j)
+                    if (cov[3 * vend + j] == io) { kite = d->kiteAreasOnVertex[3 * vend + j]; found = true; }
+            if (!found) { hm.rows_canonical = false; break; }
+            P += kite / d->areaCell[io];
+        }
+    }
     hm.eslot.assign(nE, 0);
-    hm.woeC.assign((size_t)nE * W2, 0.0);
-    hm.rows_canonical = true;
     for (int e = 0; e < nE && hm.rows_canonical; ++e) {
         if (hm.ebnd[e]) continue;
-        int k = 0, matched = 0;
-        int slot[2] = {0, 0};
-        for (int side = 0; side < 2; ++side) {
+        const double wscale = 1e-9;
+        int matched = 0;
+        int slot[2] = {0, 0}, cnt[2] = {0, 0};
+        for (int side = 0; side < 2 && hm.rows_canonical; ++side) {
             const int c = hm.coe[2 * e + side];
             const int n = hm.nEoC[c];
             int p = -1;
             for (int j = 0; j < n; ++j) if (hm.eoc[(size_t)c * W + j] == e) p = j;
             if (p < 0) { hm.rows_canonical = false; break; }
             slot[side] = p;
-            for (int j = 1; j < n; ++j) {
-                const int x = hm.eoc[(size_t)c * W + (p + j) % n];
-                double w = 0.0;
+            cnt[side] = n;
+            const double *P = &hm.rowP[(size_t)c * hm.rowS];
+            for (int j = 0; j < n; ++j) {
+                if (j == p) continue;
+                const int x = hm.eoc[(size_t)c * W + j];
+                const double rs = P[j] - P[p] + (j < p ? 1.0 : 0.0);
+                const int xo = hm.edge_n2o[x];
+                const double sgn = (side == 0 ? 1.0 : -1.0) * (coe[2 * xo] == hm.cell_n2o[c] ? 1.0 : -1.0);
+                const double w = sgn * (0.5 - rs) * d->dvEdge[xo] * hm.invDc[e];
+                bool found = false;
                 for (int q = 0; q < hm.nEoE[e]; ++q)
-                    if (hm.eoe[(size_t)e * W2 + q] == x) { w = hm.woe[(size_t)e * W2 + q]; ++matched; }
-                hm.woeC[(size_t)e * W2 + k++] = w;
+                    if (hm.eoe[(size_t)e * W2 + q] == x) {
+                        found = true;
+                        ++matched;
+                        if (std::fabs(hm.woe[(size_t)e * W2 + q] - w) > wscale * (1.0 + std::fabs(w)))
+                            hm.rows_canonical = false;
+                    }
+                if (!found && std::fabs(w) > wscale) hm.rows_canonical = false;
             }
         }
         if (!hm.rows_canonical) break;
         if (matched != hm.nEoE[e]) hm.rows_canonical = false;   // a neighbour outside the two cells
-        hm.eslot[e] = (uint16_t)(slot[0] | (slot[1] << 8));
+        hm.eslot[e] = (uint16_t)(slot[0] | (slot[1] << 4) | (cnt[0] << 8) | (cnt[1] << 12));
     }
     hm.cells_per_level = per_level;
     int64_t cu = 0, mult = 1;

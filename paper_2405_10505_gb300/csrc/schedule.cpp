@@ -4,10 +4,12 @@
 // One FB-RK(3,2) stage (Eq. fbrk32) is four passes:
 //   cell  : h_s = h0 + c tau Psi(u_in, h_in), FB average, kinetic energy K
 //   vertex: q = (zeta(u_in) + f) / h_v(FB average)
-//   eprep : per edge F = h_e u_in and q_e
+//   eprep : per edge F = h_e u_in and q_e   (or, with cell rows,
+//   trisk : per cell, each of its edges' share of the TRiSK sums and the
+//           cell's Bernoulli term K + g xi)
 //   edge  : u_s = u0 + c tau Phi(u_in, FB average)
 // Each pass covers the contiguous ranges of its step; the kinetic-energy,
-// vertex and edge-prep ranges are derived from what the edge pass reads.
+// vertex and edge-prep (trisk) ranges are derived from what the edge pass reads.
 //
 // Level pair (l, l+1) uses the paper's shrinking sets in the coarse
 // advancement (cells F^5 / F^3 / F^1, edges F_E^4 / F_E^2 / IF-1, plus the
@@ -36,7 +38,8 @@ struct AccInfo {
 
 class Builder {
 public:
-    Builder(const HostMesh &hm, const double beta[3], Schedule &s) : hm_(hm), s_(s) {
+    Builder(const HostMesh &hm, const double beta[3], bool trisk_cells, Schedule &s)
+        : hm_(hm), s_(s), trisk_cells_(trisk_cells) {
         b_[0] = beta[0]; b_[1] = beta[1]; b_[2] = beta[2];
     }
 
@@ -45,6 +48,7 @@ public:
 private:
     const HostMesh &hm_;
     Schedule &s_;
+    bool trisk_cells_;
     double b_[3];
     std::map<std::pair<int, int>, std::array<int, 6>> memo_;
 
@@ -157,10 +161,13 @@ private:
         v.kind = OP_VERT; v.stage = s; v.in_u = in_u; v.hst = hst; v.lo = vlo; v.hi = vhi;
         add_seg(v, vlo, vhi, SEG_UPD);
         s_.ops.push_back(v);
-        // edge prep
+        // edge prep over the edges and their neighbours, or the cell-side TRiSK
+        // sums over the cells of the edges
         Op p;
-        p.kind = OP_EPREP; p.stage = s; p.in_u = in_u; p.hst = hst; p.lo = plo; p.hi = phi;
-        add_seg(p, plo, phi, SEG_UPD);
+        p.kind = trisk_cells_ ? OP_TRISK : OP_EPREP; p.stage = s; p.in_u = in_u; p.hst = hst;
+        p.lo = trisk_cells_ ? klo : plo;
+        p.hi = trisk_cells_ ? khi : phi;
+        add_seg(p, p.lo, p.hi, SEG_UPD);
         s_.ops.push_back(p);
         // edge pass
         Op e;
@@ -234,72 +241,179 @@ private:
 
 }  // namespace
 
-// Algorithmic bytes of one launch: each array element its arithmetic reads or
-// writes, once, at storage size (int32 4, double 8, float 4, flag 1).
-// Gathered arrays count one read per source element, from the incidence of
-// the mesh: a pass over edges that gathers a cell array reads 2 nC/nE cell
-// elements per edge (2 cpe, cpe = nC/nE), a vertex array 2 nV/nE (2 vpe).
-// fp32: stage data, kinetic energy, PV, fluxes and coefficients in float; the
-// time level, the divergence coefficients and the correction sums in double.
+namespace {
+
+// Distinct elements that the gathers of one launch touch, counted exactly
+// over the union of its segments and memoised by segment list (the fine
+// level repeats the same ranges M times per coarse step).
+struct Touched {
+    double self = 0, slots = 0;        // elements in the segments, row slots read
+    double cells = 0, edges = 0, verts = 0;
+};
+
+class Toucher {
+public:
+    explicit Toucher(const HostMesh &hm)
+        : hm_(hm), sc_(hm.nC, 0), se_(hm.nE, 0), sv_(hm.nV, 0) {}
+
+    // kind: OP_CELL (cells -> their edges, their neighbour cells and themselves),
+    // OP_VERT (vertices -> edges, cells), OP_EPREP (edges -> cells, vertices),
+    // OP_EDGE (edges -> cells, listed neighbour edges), OP_TRISK (cells -> edges,
+    // neighbour cells and themselves, vertices)
+    const Touched &get(int kind, const std::vector<std::pair<int, int>> &ranges) {
+        auto key = std::make_pair(kind, ranges);
+        auto it = memo_.find(key);
+        if (it != memo_.end()) return it->second;
+        ++stamp_;
+        Touched t;
+        auto C = [&](int c) { if (sc_[c] != stamp_) { sc_[c] = stamp_; t.cells += 1; } };
+        auto E = [&](int e) { if (se_[e] != stamp_) { se_[e] = stamp_; t.edges += 1; } };
+        auto V = [&](int v) { if (sv_[v] != stamp_) { sv_[v] = stamp_; t.verts += 1; } };
+        const int W = hm_.maxE, W2 = hm_.maxE2;
+        for (const auto &r : ranges)
+            for (int x = r.first; x < r.second; ++x) {
+                t.self += 1;
+                switch (kind) {
+                    case OP_TRISK:
+                        C(x);
+                        t.slots += hm_.nEoC[x];
+                        for (int j = 0; j < hm_.nEoC[x]; ++j) {
+                            E(hm_.eoc[(size_t)x * W + j]);
+                            C(hm_.coc[(size_t)x * W + j]);
+                            V(hm_.rowV[(size_t)x * hm_.rowS + j]);
+                        }
+                        break;
+                    case OP_CELL:
+                        C(x);
+                        t.slots += hm_.nEoC[x];
+                        for (int j = 0; j < hm_.nEoC[x]; ++j) {
+                            E(hm_.eoc[(size_t)x * W + j]);
+                            C(hm_.coc[(size_t)x * W + j]);
+                        }
+                        break;
+                    case OP_VERT:
+                        for (int j = 0; j < 3; ++j) { E(hm_.eov[3 * (size_t)x + j]); C(hm_.cov[3 * (size_t)x + j]); }
+                        break;
+                    case OP_EPREP:
+                        C(hm_.coe[2 * (size_t)x]); C(hm_.coe[2 * (size_t)x + 1]);
+                        V(hm_.voe[2 * (size_t)x]); V(hm_.voe[2 * (size_t)x + 1]);
+                        break;
+                    case OP_EDGE:
+                        if (hm_.ebnd[x]) break;
+                        E(x);
+                        C(hm_.coe[2 * (size_t)x]);
+                        C(hm_.coe[2 * (size_t)x + 1]);
+                        t.slots += hm_.nEoE[x];
+                        for (int j = 0; j < hm_.nEoE[x]; ++j) E(hm_.eoe[(size_t)x * W2 + j]);
+                        break;
+                    default: break;
+                }
+            }
+        return memo_.emplace(key, t).first->second;
+    }
+
+private:
+    const HostMesh &hm_;
+    std::vector<int> sc_, se_, sv_;
+    int stamp_ = 0;
+    std::map<std::pair<int, std::vector<std::pair<int, int>>>, Touched> memo_;
+};
+
+}  // namespace
+
+// Algorithmic bytes of one launch: every array element that its arithmetic
+// reads or writes, once, at storage size (int32 4, double 8, float 4, flag 1,
+// 16-byte records 16), with gathered arrays counted over the distinct
+// elements the launch touches (exact, from the mesh incidence).  A padded
+// row counts at its stored width.  FP32: stage data, kinetic energy, PV,
+// edge records and coefficients in float; the time level, 1/A and the
+// correction sums in double.
 void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
-    std::vector<double> pc(hm.nC + 1, 0.0), pe(hm.nE + 1, 0.0);
-    for (int i = 0; i < hm.nC; ++i) pc[i + 1] = pc[i] + hm.nEoC[i];
-    for (int e = 0; e < hm.nE; ++e) pe[e + 1] = pe[e] + hm.nEoE[e];
-    const double cpe = (double)hm.nC / hm.nE, vpe = (double)hm.nV / hm.nE;
+    Toucher tch(hm);
     const double R = fp32 ? 4.0 : 8.0;        // stage / scratch element
     const double C = fp32 ? 4.0 : 8.0;        // coefficient element
+    const bool vortex = (forcing & FBLTS_FORCE_VORTEX) != 0;
     for (Op &op : s.ops) {
         double b = 0.0;
+        std::vector<std::pair<int, int>> all;
+        for (int k = 0; k < op.nseg; ++k)
+            if (op.seg[k].end > op.seg[k].begin) all.emplace_back(op.seg[k].begin, op.seg[k].end);
+        auto per_mode = [&](double n, int mode, bool cell) {
+            double x = 0.0;
+            if (mode == SEG_UPD)   // stage inputs at the element, stage output (+ FB average for cells)
+                x = cell ? n * R * (3 + (op.stage == 3 ? 1 : 0)) : n * 2 * R;
+            if (mode == SEG_INPLACE) {
+                if (cell) x = fp32 ? n * (16 + 8 + 4 + 4 + 4 + (op.stage == 3 ? 4 : 0)) : n * (16 + 8 + 8);
+                else x = fp32 ? n * (16 + 4) : n * 16;
+            }
+            if (mode == SEG_ACC_SET) x = n * 8;
+            if (mode == SEG_ACC_ADD) x = n * 16;
+            return x;
+        };
         switch (op.kind) {
-            case OP_CELL:
-                for (int k = 0; k < op.nseg; ++k) {
-                    const Seg &g = op.seg[k];
-                    const double n = g.end - g.begin, slots = pc[g.end] - pc[g.begin];
-                    if (fp32) {
-                        // nEoC, 1/A, K | signed edge row, u_in and the 16-byte edge record
-                        // {l_e, d_e l_e/4, H_e} (an edge has 2 cells)
-                        b += n * (4 + 8 + 4) + slots * (4 + 2 + 8);
-                        if (g.mode == SEG_KONLY) continue;
-                        b += n * 4 + slots * 4;                      // xi_in | coc
-                    } else {
-                        // nEoC, K out | eoc, cKE, u_in (an edge is gathered by 2 cells)
-                        b += n * (4 + 8) + slots * (4 + 8 + 4);
-                        if (g.mode == SEG_KONLY) continue;
-                        b += n * 8 + slots * (4 + 8);                // h_in | coc, cDiv
+            case OP_CELL: {
+                if (all.empty()) break;
+                // cells: nEoC, 1/A, K out; rows (signed edge, neighbour cell);
+                // edges: u_in and (fp32) the 16-byte record {l, d l / 4, H_e}
+                // or (fp64) the per-slot coefficients; xi / h at the cells
+                bool konly = true;
+                for (int k = 0; k < op.nseg; ++k) konly = konly && op.seg[k].mode == SEG_KONLY;
+                const Touched &t = tch.get(OP_CELL, all);
+                b += t.self * (4 + (fp32 ? 8 : 0) + R) + t.slots * 4 + t.edges * (R + (fp32 ? 16 : 0));
+                if (!fp32) b += t.slots * C;                           // cKE
+                if (!konly) b += t.slots * (4 + (fp32 ? 0 : C)) + t.cells * R;   // coc (+ cDiv), h_in
+                for (int k = 0; k < op.nseg; ++k)
+                    b += per_mode(op.seg[k].end - op.seg[k].begin, op.seg[k].mode, true);
+            } break;
+            case OP_VERT: {
+                const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
+                const Touched &t = tch.get(OP_VERT, r);
+                // eov, cov, cVort, cKite, f, (fp32) H_v, q out | u_in, hst
+                b = t.self * (3 * (4 + 4 + C + C) + C + (fp32 ? 4 : 0) + R) + t.edges * R + t.cells * R;
+            } break;
+            case OP_EPREP: {
+                const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
+                const Touched &t = tch.get(OP_EPREP, r);
+                // coe, voe, u_in, (fp32) l_e, H_e and the 16-byte record out,
+                // (fp64) ebnd and F, q_e, F q_e out | hst at cells, q at vertices
+                b = t.self * (16 + R + (fp32 ? 4 + 4 + 16 : 1 + 3 * R)) + t.cells * R + t.verts * R;
+            } break;
+            case OP_TRISK: {
+                const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
+                const Touched &t = tch.get(OP_TRISK, r);
+                // cells: nEoC, K, rows {signed edge, kite prefix, neighbour cell,
+                // vertex} at their stored width, (vortex) p_s, one 16-byte share
+                // out per slot | edges: u_in, {l, d l / 4, H_e} | hst at the cells
+                // and their neighbours | q at the vertices
+                b = t.self * (4 + R + hm.rowS * 16 + (vortex ? R : 0)) + t.slots * 16 + t.edges * (R + 16) +
+                    t.cells * R + t.verts * R;
+            } break;
+            case OP_EDGE: {
+                if (all.empty()) break;
+                if (fp32 && hm.rows_canonical) {
+                    // ebnd, 1/d_e, the two cells' 16-byte shares
+                    for (int k = 0; k < op.nseg; ++k) {
+                        const double n = op.seg[k].end - op.seg[k].begin;
+                        b += n * (1 + 4 + 32) + per_mode(n, op.seg[k].mode, false);
+                        if (forcing) b += n * (R + 4 + 3 * R);   // u_in, H_e, wind, C_W
                     }
-                    if (g.mode == SEG_UPD) b += n * R * (3 + (op.stage == 3 ? 1 : 0));
-                    if (g.mode == SEG_INPLACE)
-                        b += n * (fp32 ? (8 + 8 + 8 + 4 + 4 + 4) : (8 + 8 + 8)) + n * (op.stage == 3 ? R : 0);
-                    if (g.mode == SEG_ACC_SET) b += n * 8;
-                    if (g.mode == SEG_ACC_ADD) b += n * 16;
+                    break;
                 }
-                break;
-            case OP_VERT:
-                b = (double)(op.hi - op.lo) * (3 * (4 + 4 + C + C) + C + (fp32 ? 4 : 0) + 1.5 * R + 0.5 * R + R);
-                break;
-            case OP_EPREP:   // fp32 writes the 16-byte record {F, q_e, u, 0}
-                b = (double)(op.hi - op.lo) * (17 + (fp32 ? 4 : 0) + R + R * 2 * cpe + R * 2 * vpe + (fp32 ? 16 : 3 * R));
-                break;
-            case OP_EDGE:
-                for (int k = 0; k < op.nseg; ++k) {
-                    const Seg &g = op.seg[k];
-                    const double n = g.end - g.begin, slots = pe[g.end] - pe[g.begin];
-                    // ebnd, nEoE, neighbour records (fp32: {F, q_e, u} 16 B; fp64: F, q_e, F q_e),
-                    // coe, invDc, K and hst at the cells (+ bottom in double); neighbours: an
-                    // index and a weight per slot, or (rows) the two cells' edge rows, each row
-                    // shared by the cell's edges, plus the two slots
-                    b += n * (1 + 4 + (fp32 ? 16 : 3 * R) + 8 + C + 2 * R * 2 * cpe + (fp32 ? 0 : 8 * 2 * cpe));
-                    if (fp32 && hm.rows_canonical)
-                        b += n * (2 + 2 * cpe * (4 + 4 * (pc[hm.nC] / hm.nC))) + slots * C;
-                    else
-                        b += slots * (4 + C);
-                    if (g.mode == SEG_UPD) b += n * 2 * R;
-                    if (g.mode == SEG_INPLACE) b += n * (fp32 ? (8 + 8 + 4) : 16);
-                    if (g.mode == SEG_ACC_SET) b += n * 8;
-                    if (g.mode == SEG_ACC_ADD) b += n * 16;
-                    if (forcing) b += n * ((fp32 ? 0 : R) + 3 * R + (fp32 ? 4 : 0) + R * 2 * cpe);
+                const Touched &t = tch.get(OP_EDGE, all);
+                // explicit neighbour lists: ebnd, coe, invDc | K, hst at cells (+ bottom
+                // in double) | neighbour records | nEoE, eoe, woe
+                b += t.self * (1 + 8 + C) + t.cells * (2 * R + (fp32 ? 0 : 8));
+                if (fp32) b += t.edges * 16;                  // {l F, q_e, l u} (own q_e included)
+                else b += t.edges * 2 * R + t.self * R;       // F, F q_e at the neighbours, own q_e
+                b += t.self * 4 + t.slots * (4 + C);
+                if (forcing) {
+                    // u_in (fp64: at the neighbours too), H_e (fp32), wind, C_W; surface pressure at cells
+                    b += fp32 ? t.self * (R + 4 + 3 * R) : t.self * 3 * R + t.edges * R;
+                    if (vortex) b += t.cells * R;
                 }
-                break;
+                for (int k = 0; k < op.nseg; ++k)
+                    b += per_mode(op.seg[k].end - op.seg[k].begin, op.seg[k].mode, false);
+            } break;
             case OP_SAVE: {
                 const double big = fp32 ? (16 + 3 * 8) : 64;   // h^n copy + 3 stage copies
                 b = big * (op.c_if1_hi - op.c_if1_lo) + 16.0 * (op.c_if12_hi - op.c_if1_hi) +
@@ -315,8 +429,7 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
                 break;
             case OP_FORCING:
                 if (forcing)
-                    b = (double)hm.nE * (16 + 3 * R + ((forcing & FBLTS_FORCE_VORTEX) ? 16 : 0)) +
-                        (double)hm.nC * (R + ((forcing & FBLTS_FORCE_VORTEX) ? 16 : 0));
+                    b = (double)hm.nE * (16 + 3 * R + (vortex ? 16 : 0)) + (double)hm.nC * (R + (vortex ? 16 : 0));
                 break;
             case OP_STEP_END: b = 16; break;
             default: break;
@@ -325,12 +438,12 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
     }
 }
 
-void build_schedule(const HostMesh &hm, double dt, const double beta[3], Schedule &s) {
+void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, Schedule &s) {
     s.ops.clear();
     Op fz;
     fz.kind = OP_FORCING;
     s.ops.push_back(fz);
-    Builder b(hm, beta, s);
+    Builder b(hm, beta, trisk_cells, s);
     b.top(dt);
     Op se;
     se.kind = OP_STEP_END;

@@ -28,7 +28,10 @@ CASES = {
 def test_fp32_parity_with_fp64_oracle(name):
     make, nsteps, M = CASES[name]
     s = make()
-    st = make_state(s, M=M, precision=fb.FP32_TENDENCY)
+    mesh = fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M if M is None else M)
+    # these meshes carry the kite-fraction TRiSK weights: the edge pass reads the cell rows
+    assert fb.mesh_get_info(mesh).flags & 1
+    st = make_state(s, M=M, precision=fb.FP32_TENDENCY, mesh=mesh)
     fb.lts_advance(st, nsteps)
     h, u = fb.state_read(st)
     m = oracle.Mesh.from_scenario(s)
@@ -58,3 +61,21 @@ def test_fp32_reproducible_and_graph_equals_stream():
         out.append(fb.state_read(st))
     for o in out[1:]:
         assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
+
+
+def test_fp32_explicit_neighbour_lists():
+    """Weights that are not the kite-fraction form (perturbed by 1e-6
+    relative) take the explicit-list edge pass; the oracle runs the same
+    weights."""
+    s = scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3)
+    rng = np.random.default_rng(7)
+    s.mesh.weightsOnEdge = s.mesh.weightsOnEdge * (1.0 + 1e-6 * rng.uniform(-1, 1, s.mesh.weightsOnEdge.shape))
+    mesh = fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M)
+    assert not (fb.mesh_get_info(mesh).flags & 1)
+    st = make_state(s, precision=fb.FP32_TENDENCY, mesh=mesh)
+    fb.lts_advance(st, 60)
+    h, u = fb.state_read(st)
+    ho, uo = oracle.fblts(oracle.Mesh.from_scenario(s), oracle.scenario_params(s), s.level, s.M, s.h0, s.u0,
+                          s.dt, 60)
+    dh, du = rel_errors(h, u, ho, uo)
+    assert dh <= 1e-6 and du <= 1e-5, (dh, du)
