@@ -189,6 +189,23 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     addf(slot_major(hm.cVort, nV, 3), &dm.cVort32);
     addf(slot_major(hm.cKite, nV, 3), &dm.cKite32);
     addf(hm.fV, &dm.fV32);
+    {   // FP32 vertex pass: {e0, e1, e2, c0}, {c1, c2}, {t d / A_v x3, f} per vertex
+        std::vector<int> i4((size_t)nV * 4), i2((size_t)nV * 2);
+        std::vector<double> f4((size_t)nV * 4);
+        for (int v = 0; v < nV; ++v) {
+            for (int j = 0; j < 3; ++j) {
+                i4[4 * (size_t)v + j] = hm.eov[3 * (size_t)v + j];
+                f4[4 * (size_t)v + j] = hm.cVort[3 * (size_t)v + j];
+            }
+            i4[4 * (size_t)v + 3] = hm.cov[3 * (size_t)v];
+            i2[2 * (size_t)v] = hm.cov[3 * (size_t)v + 1];
+            i2[2 * (size_t)v + 1] = hm.cov[3 * (size_t)v + 2];
+            f4[4 * (size_t)v + 3] = hm.fV[v];
+        }
+        addi(i4, (const int **)&dm.vI4);
+        addi(i2, (const int **)&dm.vI2);
+        addf(f4, (const float **)&dm.vCf);
+    }
     addi(slot_major(hm.eocS, nC, mE), &dm.eocS);
     addf(hm.dvE, &dm.dv32);
     addf(hm.keE, &dm.ke32);
@@ -374,6 +391,9 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         if (a == A_FQU) return (m->dm.rowS ? 8 : 4) * (size_t)nE;
         return arr_is_cell(a) ? (size_t)nC : (arr_is_vert(a) ? (size_t)nV : (size_t)nE);
     };
+    // the launch list of one coarse step and its algorithmic bytes
+    build_schedule(hm, p->dt, p->beta, f32 && m->dm.rowS != 0, s->sched);
+    schedule_bytes(hm, p->forcing, f32, s->sched);
     // every allocation in order; the sizing pass and the carving pass walk the same list
     size_t szc = sizeof(double) * (size_t)nC, sze = sizeof(double) * (size_t)nE;
     std::vector<size_t> plan;
@@ -384,6 +404,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         plan.push_back(4 * (size_t)nC); plan.push_back(4 * (size_t)nE);            // shadows
         plan.push_back(4 * (size_t)nC); plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nV);  // depths
         plan.push_back(16 * (size_t)nE);                                            // per-edge record
+        plan.push_back(16 * (size_t)nV);                                            // per-vertex record
         plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nE);
         plan.push_back(4 * (size_t)nC);                                             // forcing (float)
     }
@@ -424,7 +445,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     s->fz.cw = (double *)got[gi++];
     s->fz.ps = (double *)got[gi++];
     float *H32 = nullptr, *He32 = nullptr, *Hv32 = nullptr;
-    float4 *estat = nullptr;
+    float4 *estat = nullptr, *vkh = nullptr;
     if (f32) {
         s->arr.xi32 = (float *)got[gi++];
         s->arr.u32 = (float *)got[gi++];
@@ -432,6 +453,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         He32 = (float *)got[gi++];
         Hv32 = (float *)got[gi++];
         estat = (float4 *)got[gi++];
+        vkh = (float4 *)got[gi++];
         s->fz.windN32 = (float *)got[gi++];
         s->fz.windT32 = (float *)got[gi++];
         s->fz.cw32 = (float *)got[gi++];
@@ -459,8 +481,8 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         }
     }
     if (st == FBLTS_OK && f32) {
-        s->dm.H32 = H32; s->dm.He32 = He32; s->dm.Hv32 = Hv32; s->dm.estat = estat;
-        if (launch_fp32_depths(s->dm, H32, He32, Hv32, estat, s->st) != cudaSuccess ||
+        s->dm.H32 = H32; s->dm.He32 = He32; s->dm.Hv32 = Hv32; s->dm.estat = estat; s->dm.vKh = vkh;
+        if (launch_fp32_depths(s->dm, H32, He32, Hv32, estat, vkh, s->st) != cudaSuccess ||
             launch_fp32_shadows(s->dm, s->arr, s->st) != cudaSuccess) {
             set_error("state_init: FP32 setup failed");
             st = FBLTS_E_CUDA;
@@ -475,8 +497,6 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     fz.rho_air = p->rho_air > 0 ? p->rho_air : 1.225;
     for (int k = 0; k < 9; ++k) fz.vx[k] = p->vortex[k];
     fz.t0 = p->t0; fz.dt = p->dt; fz.step = s->d_step;
-    build_schedule(hm, p->dt, p->beta, f32 && m->dm.rowS != 0, s->sched);
-    schedule_bytes(hm, p->forcing, p->precision == FBLTS_FP32_TENDENCY, s->sched);
     if (cudaStreamSynchronize(s->st) != cudaSuccess) {
         set_error("state_init: %s", cudaGetErrorString(cudaGetLastError()));
         fblts_state_destroy(s);

@@ -31,8 +31,8 @@ struct PrepArgs32 {
 };
 
 // Cell-side TRiSK pass: per slot of each cell, the share {t, s_v, B_i, xi*_i}
-// of the cell in its edge's Coriolis and tangential sums (see trisk32_body),
-// written to half[2 e + side] (side 0 = first cell of e).
+// of the cell in its edge's momentum tendency (trisk32_body), written to
+// half[2 e + side] (side 0 = first cell of e).
 struct TriskArgs32 {
     int lo, hi;
     const float *u_in, *hst, *K, *q;
@@ -135,36 +135,60 @@ inline IfArgs32 if_args32(const Op &op, const DevArrays &arr, const DevMesh &m) 
 // (1/A_i) sum_j (d_e l_e / 4) u_e^2.  NMAX bounds the edges of a cell so the
 // row is loaded before the dependent gathers; the static per-edge data
 // {l_e, d_e l_e / 4, H_e} is one 16-byte gather.
-template <int NMAX>
+template <int NMAX, bool ROWS>
 FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     const int mode = seg_mode(a.segs, i);
     if (mode == SEG_NONE) return;
     const int n = m.nEoC[i];
-    const int nC = m.nC;
     int er[NMAX], nb[NMAX];
-    FB_UNROLL
-    for (int j = 0; j < NMAX; ++j) {
-        er[j] = 0;
-        nb[j] = i;
-        if (j < n) {
-            er[j] = m.eocS[j * nC + i];
-            nb[j] = m.coc[j * nC + i];
-        }
-    }
     float ue[NMAX], sdv[NMAX], kw[NMAX], He[NMAX];
-    FB_UNROLL
-    for (int j = 0; j < NMAX; ++j) {
-        ue[j] = 0.f;
-        sdv[j] = 0.f;
-        kw[j] = 0.f;
-        He[j] = 0.f;
-        if (j < n) {
+    if constexpr (ROWS) {
+        // cell-major rows padded with valid indices: vector loads, then every
+        // gather unconditionally; the padding is masked
+        static_assert(NMAX % 4 == 0, "row width");
+        const int4 *e4 = reinterpret_cast<const int4 *>(m.rowE + (size_t)i * NMAX);
+        const int4 *n4 = reinterpret_cast<const int4 *>(m.rowN + (size_t)i * NMAX);
+        FB_UNROLL
+        for (int q = 0; q < NMAX / 4; ++q) {
+            const int4 te = e4[q], tn = n4[q];
+            er[4 * q] = te.x; er[4 * q + 1] = te.y; er[4 * q + 2] = te.z; er[4 * q + 3] = te.w;
+            nb[4 * q] = tn.x; nb[4 * q + 1] = tn.y; nb[4 * q + 2] = tn.z; nb[4 * q + 3] = tn.w;
+        }
+        FB_UNROLL
+        for (int j = 0; j < NMAX; ++j) {
             const int e = er[j] < 0 ? ~er[j] : er[j];
-            ue[j] = a.u_in[e];
+            const float u = a.u_in[e];
             const float4 st = m.estat[e];
+            ue[j] = j < n ? u : 0.f;
             kw[j] = st.y;
             He[j] = st.z;
-            sdv[j] = er[j] < 0 ? st.x : -st.x;    // -n_{e,i} l_e
+            sdv[j] = j < n ? (er[j] < 0 ? st.x : -st.x) : 0.f;    // -n_{e,i} l_e
+        }
+    } else {
+        const int nC = m.nC;
+        FB_UNROLL
+        for (int j = 0; j < NMAX; ++j) {
+            er[j] = 0;
+            nb[j] = i;
+            if (j < n) {
+                er[j] = m.eocS[j * nC + i];
+                nb[j] = m.coc[j * nC + i];
+            }
+        }
+        FB_UNROLL
+        for (int j = 0; j < NMAX; ++j) {
+            ue[j] = 0.f;
+            sdv[j] = 0.f;
+            kw[j] = 0.f;
+            He[j] = 0.f;
+            if (j < n) {
+                const int e = er[j] < 0 ? ~er[j] : er[j];
+                ue[j] = a.u_in[e];
+                const float4 st = m.estat[e];
+                kw[j] = st.y;
+                He[j] = st.z;
+                sdv[j] = er[j] < 0 ? st.x : -st.x;    // -n_{e,i} l_e
+            }
         }
     }
     float ke = 0.f;
@@ -206,16 +230,16 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     }
 }
 
-// Vertex v: q_v = (zeta_v + f_v) / (H_v + sum_j kite xi / A_v)  (Eq. trisk_vorticity).
+// Vertex v: q_v = (zeta_v + f_v) / (H_v + sum_j kite xi / A_v)  (Eq. trisk_vorticity),
+// from three 16-byte and one 8-byte record per vertex.
 FB_HD void vert32_body(const DevMesh &m, const VertArgs32 &a, int v) {
-    const int nV = m.nV;
-    float z = 0.f, xv = 0.f;
-    FB_UNROLL
-    for (int j = 0; j < 3; ++j) {
-        z += m.cVort32[j * nV + v] * a.u_in[m.eov[j * nV + v]];
-        xv += m.cKite32[j * nV + v] * a.hst[m.cov[j * nV + v]];
-    }
-    a.q[v] = (z + m.fV32[v]) / (m.Hv32[v] + xv);
+    const int4 ix = m.vI4[v];
+    const int2 c12 = m.vI2[v];
+    const float4 cf = m.vCf[v];
+    const float4 kh = m.vKh[v];
+    const float z = cf.x * a.u_in[ix.x] + cf.y * a.u_in[ix.y] + cf.z * a.u_in[ix.z];
+    const float xv = kh.x * a.hst[ix.w] + kh.y * a.hst[c12.x] + kh.z * a.hst[c12.y];
+    a.q[v] = (z + cf.w) / (kh.w + xv);
 }
 
 // Edge e: {l_e F_e, q_e, l_e u_e, 0} with F_e = (H_e + (xi_c0 + xi_c1)/2) u_e,
@@ -307,6 +331,45 @@ FB_HD void trisk32_body(const DevMesh &m, const TriskArgs32 &a, const DevForcing
     }
 }
 
+// Phi_e from the two cells' shares {t, s_v, B, xi*} (trisk32_shares):
+// Phi_e = [(t_0 + t_1)/2 - (B_1 - B_0)] / d_e plus, with forcing, the wind
+// stress and quadratic drag (Eq. hurricane_model) with v_e = (s_v0 + s_v1) / d_e
+// and h_e = H_e + (xi*_0 + xi*_1)/2; the surface pressure is inside B.
+template <bool FORCING>
+FB_HD float phi_from_shares(const DevMesh &m, const float *u_in, const DevForcing &fz, int e, float4 h0, float4 h1) {
+    const float idc = m.invDc32[e];
+    float phi = idc * (0.5f * (h0.x + h1.x) - (h1.z - h0.z));
+    if (FORCING) {
+        const float vt = idc * (h0.y + h1.y);
+        const float ue = u_in[e];
+        const float he = m.He32[e] + 0.5f * (h0.w + h1.w);
+        if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
+            const float dn = fz.windN32[e] - ue, dt = fz.windT32[e] - vt;
+            phi += fz.cw32[e] * sqrtf(dn * dn + dt * dt) * dn / he;
+        }
+        if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue / he;
+    }
+    return phi;
+}
+
+// The edge's update by segment mode: stage value u0 + c tau Phi (float), in
+// place u += c tau Phi (double, with the float shadow), or the correction sum.
+// No-flow edges take u = 0 and contribute 0.
+template <class A>
+FB_HD void edge32_apply(const A &a, int mode, int e, bool bnd, float phi) {
+    switch (mode) {
+        case SEG_UPD: a.us_out[e] = bnd ? 0.f : a.u0[e] + (float)a.cdt * phi; break;
+        case SEG_INPLACE: {
+            const double un = bnd ? 0.0 : a.u_state[e] + a.cdt * (double)phi;
+            a.u_state[e] = un;
+            a.u_shadow[e] = (float)un;
+        } break;
+        case SEG_ACC_SET: a.acc[e] = (double)phi; break;
+        case SEG_ACC_ADD: a.acc[e] += (double)phi; break;
+        default: break;
+    }
+}
+
 // Edge e: Phi_e in float (the pressure gradient g (xi_c1 - xi_c0) / d_e needs
 // no cancellation of large depths), stage value u_s = u0 + c tau Phi, in
 // place u += c tau Phi in double, or the correction sum in double.  SHARES:
@@ -316,21 +379,18 @@ template <bool SHARES, bool FORCING>
 FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &fz, int e) {
     const int mode = seg_mode(a.segs, e);
     if (mode == SEG_NONE) return;
+    const bool bnd = m.ebnd[e] != 0;
     float phi = 0.f;
-    if (!m.ebnd[e]) {
-        const float idc = m.invDc32[e];
-        float vt = 0.f, xsum = 0.f;
+    if (!bnd) {
         if constexpr (SHARES) {
-            const float4 h0 = a.half[2 * e], h1 = a.half[2 * e + 1];
-            phi = idc * (0.5f * (h0.x + h1.x) - (h1.z - h0.z));
-            vt = idc * (h0.y + h1.y);
-            xsum = h0.w + h1.w;
+            phi = phi_from_shares<FORCING>(m, a.u_in, fz, e, a.half[2 * e], a.half[2 * e + 1]);
         } else {
             // explicit neighbour list; the weights are W_{e,e'} / l_{e'}
+            const float idc = m.invDc32[e];
             const int nE = m.nE, n = m.nEoE[e];
             const int c0 = m.coe0[e], c1 = m.coe1[e];
             const float qself = a.fqu[e].y;
-            float cor = 0.f;
+            float cor = 0.f, vt = 0.f;
             for (int j = 0; j < n; ++j) {
                 const int x = m.eoe[j * nE + e];
                 const float w = m.woe32[j * nE + e];
@@ -341,30 +401,19 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
             const float x0c = a.hst[c0], x1c = a.hst[c1];
             const float grad = (a.K[c1] - a.K[c0]) + a.g * (x1c - x0c);
             phi = cor - grad * idc;
-            xsum = x0c + x1c;
-            if (FORCING && (fz.flags & FBLTS_FORCE_VORTEX)) phi -= (fz.ps32[c1] - fz.ps32[c0]) * idc / (float)fz.rho0;
-        }
-        if (FORCING) {
-            const float ue = a.u_in[e];
-            const float he = m.He32[e] + 0.5f * xsum;
-            if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
-                const float dn = fz.windN32[e] - ue, dt = fz.windT32[e] - vt;
-                phi += fz.cw32[e] * sqrtf(dn * dn + dt * dt) * dn / he;
+            if (FORCING) {
+                const float ue = a.u_in[e];
+                const float he = m.He32[e] + 0.5f * (x0c + x1c);
+                if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
+                    const float dn = fz.windN32[e] - ue, dt = fz.windT32[e] - vt;
+                    phi += fz.cw32[e] * sqrtf(dn * dn + dt * dt) * dn / he;
+                }
+                if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue / he;
+                if (fz.flags & FBLTS_FORCE_VORTEX) phi -= (fz.ps32[c1] - fz.ps32[c0]) * idc / (float)fz.rho0;
             }
-            if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue / he;
         }
     }
-    switch (mode) {
-        case SEG_UPD: a.us_out[e] = m.ebnd[e] ? 0.f : a.u0[e] + (float)a.cdt * phi; break;
-        case SEG_INPLACE: {
-            const double un = m.ebnd[e] ? 0.0 : a.u_state[e] + a.cdt * (double)phi;
-            a.u_state[e] = un;
-            a.u_shadow[e] = (float)un;
-        } break;
-        case SEG_ACC_SET: a.acc[e] = (double)phi; break;
-        case SEG_ACC_ADD: a.acc[e] += (double)phi; break;
-        default: break;
-    }
+    edge32_apply(a, mode, e, bnd, phi);
 }
 
 // Saves h^n, u^n (double) on IF-1 u IF-2 and the uncorrected IF-1 stage data (float).

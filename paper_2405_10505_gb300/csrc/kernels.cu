@@ -73,11 +73,11 @@ __global__ void __launch_bounds__(TPB) forcing_pass(DevMesh m, DevForcing fz) {
     forcing_body(m, fz, time, t);
 }
 
-template <int NMAX>
+template <int NMAX, bool ROWS>
 __global__ void __launch_bounds__(TPB) cell32_pass(DevMesh m, CellArgs32 a) {
     wait_predecessor();
     const int i = a.lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.hi) cell32_body<NMAX>(m, a, i);
+    if (i < a.hi) cell32_body<NMAX, ROWS>(m, a, i);
 }
 
 __global__ void __launch_bounds__(TPB) vert32_pass(DevMesh m, VertArgs32 a) {
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(TPB) forcing32_pass(DevMesh m, DevForcing fz) 
 // resting depth seen by the FP32 path: H per cell, mean over the present cells
 // of an edge (also in the per-edge record {l_e, d_e l_e / 4, H_e, 0}),
 // kite-weighted mean at a vertex
-__global__ void fp32_depths(DevMesh m, float *H32, float *He32, float *Hv32, float4 *estat) {
+__global__ void fp32_depths(DevMesh m, float *H32, float *He32, float *Hv32, float4 *estat, float4 *vkh) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < m.nC) H32[t] = (float)(-m.bottom[t]);
     if (t < m.nE) {
@@ -147,6 +147,7 @@ __global__ void fp32_depths(DevMesh m, float *H32, float *He32, float *Hv32, flo
         double s = 0.0;
         for (int j = 0; j < 3; ++j) s += m.cKite[j * m.nV + t] * (-m.bottom[m.cov[j * m.nV + t]]);
         Hv32[t] = (float)s;
+        vkh[t] = make_float4((float)m.cKite[t], (float)m.cKite[m.nV + t], (float)m.cKite[2 * m.nV + t], (float)s);
     }
 }
 
@@ -263,9 +264,12 @@ static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &
         case OP_CELL: {
             if (op.hi <= op.lo) return cudaSuccess;
             const CellArgs32 a = cell_args32(op, arr, m);
-            if (m.maxE <= 6) CK_L(pdl(cell32_pass<6>, nblk(op.hi - op.lo), TPB, st, m, a));
-            else if (m.maxE <= 8) CK_L(pdl(cell32_pass<8>, nblk(op.hi - op.lo), TPB, st, m, a));
-            else CK_L(pdl(cell32_pass<12>, nblk(op.hi - op.lo), TPB, st, m, a));
+            const int nb = nblk(op.hi - op.lo);
+            if (m.rowS == 8) CK_L(pdl(cell32_pass<8, true>, nb, TPB, st, m, a));
+            else if (m.rowS == 12) CK_L(pdl(cell32_pass<12, true>, nb, TPB, st, m, a));
+            else if (m.maxE <= 6) CK_L(pdl(cell32_pass<6, false>, nb, TPB, st, m, a));
+            else if (m.maxE <= 8) CK_L(pdl(cell32_pass<8, false>, nb, TPB, st, m, a));
+            else CK_L(pdl(cell32_pass<12, false>, nb, TPB, st, m, a));
         } break;
         case OP_VERT:
             if (op.hi <= op.lo) return cudaSuccess;
@@ -322,9 +326,9 @@ static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &
 }
 
 cudaError_t launch_fp32_depths(const DevMesh &m, float *H32, float *He32, float *Hv32, float4 *estat,
-                               cudaStream_t st) {
+                               float4 *vkh, cudaStream_t st) {
     const int n = m.nE > m.nV ? (m.nE > m.nC ? m.nE : m.nC) : (m.nV > m.nC ? m.nV : m.nC);
-    fp32_depths<<<nblk(n), TPB, 0, st>>>(m, H32, He32, Hv32, estat);
+    fp32_depths<<<nblk(n), TPB, 0, st>>>(m, H32, He32, Hv32, estat, vkh);
     return cudaGetLastError();
 }
 

@@ -218,3 +218,34 @@ def nested_disk_case(nx=48, ny=48, dc=10e3, H=1000.0, f=1e-4, amp=1.0, efold=60e
     return Scenario(name=f"nested_hex{nx}x{ny}", mesh=mesh, bottom=np.full(mesh.nCells, -H),
                     fVertex=np.full(mesh.nVertices, f), h0=h0, u0=np.zeros(mesh.nEdges),
                     level=level, M=list(M), dt=dt)
+
+
+def jittered_voronoi_case(k=38, L=300e3, jitter=0.45, H=1000.0, f=1e-4, amp=1.0, efold=40e3,
+                          fine_radius=70e3, M=2, seed=3):
+    """Irregular Voronoi mesh: a k x k grid of generators in a square box,
+    each moved by a seeded uniform offset of up to ``jitter`` spacings, Qhull
+    Delaunay, hull cells dropped.  Cells have 3 to about 11 edges and many
+    triangles are obtuse (negative kites).  Flat depth ``H``, a Gaussian bump
+    at the centre; with ``fine_radius`` a central disk is level 1 (separated).
+    """
+    from scipy.spatial import Delaunay
+    from .mesh import build_from_triangles
+    rng = _rng(seed)
+    dx = L / k
+    x, y = np.meshgrid(np.arange(k) * dx, np.arange(k) * dx)
+    pts = np.stack([x.ravel(), y.ravel()], 1) + rng.uniform(-jitter, jitter, (k * k, 2)) * dx
+    full = build_from_triangles(pts, Delaunay(pts).simplices, period=None)
+    mesh = finalize(apply_cell_mask(full, np.ones(full.nCells, bool)))
+    r2 = (mesh.xCell - L / 2) ** 2 + (mesh.yCell - L / 2) ** 2
+    h0 = H + amp * np.exp(-r2 / efold ** 2)
+    level = np.zeros(mesh.nCells, np.int32)
+    Ms = []
+    if fine_radius:
+        level[r2 < fine_radius ** 2] = 1
+        level = enforce_level_separation(mesh, level).astype(np.int32)
+        Ms = [M]
+    interior = (mesh.cellsOnEdge >= 0).all(1)
+    dt = 0.3 * float(mesh.dcEdge[interior].min()) / np.sqrt(G * H) * (M if fine_radius else 1)
+    return Scenario(name=f"jittered_voronoi_{mesh.nCells}", mesh=mesh, bottom=np.full(mesh.nCells, -H),
+                    fVertex=np.full(mesh.nVertices, f), h0=h0, u0=np.zeros(mesh.nEdges), level=level,
+                    M=Ms, dt=float(dt), forcing=Forcing(wind_u=0.0, wind_v=0.0, cd=0.0, wind_stress=False))

@@ -31,6 +31,8 @@ CASES = {
     "shelf_forced_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3), 100, None),
     "nested_3level": (lambda: scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3)), 40, None),
     "shelf_vortex_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3, vortex=True), 60, None),
+    # irregular cells of 3..11 edges (12-slot rows, obtuse triangles), 2 levels
+    "jittered_voronoi_m2": (lambda: scenario.jittered_voronoi_case(), 60, None),
 }
 
 
