@@ -174,15 +174,25 @@ def cell_updates_per_step(s):
     return cu
 
 
+def reference_sample(workload, s):
+    """The workload the oracle times per step: the workload itself, or for the
+    2M-cell basin (about 100 s per oracle coarse step) its 1/8-length sample."""
+    if workload == "basin":
+        ws, _ = make_workload("basin_small")
+        return ws, "basin_small (1/8-length sample of the basin: same recipe, Ly 1200 km)"
+    return s, workload
+
+
 def run_reference(args, s, desc, rank):
     if rank != 0:
         return
+    ws, sample_name = reference_sample(args.workload, s)
     for _ in range(args.warmup):
-        oracle_sample(s, budget_s=0.0)
-    cu = cell_updates_per_step(s)
+        oracle_sample(ws, budget_s=0.0)
+    cu = cell_updates_per_step(ws)
     times = []
     for k in range(args.steps):
-        n, el, _, _ = oracle_sample(s, budget_s=0.0)
+        n, el, _, _ = oracle_sample(ws, budget_s=0.0)
         times.append(el / n)
     ms = 1000.0 * statistics.mean(times)
     v = cu / (ms / 1000.0)
@@ -191,9 +201,34 @@ def run_reference(args, s, desc, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "cells": int(s.mesh.nCells)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} whole coarse steps of {args.workload}, single-thread C oracle"},
+                             "sample": f"{args.steps} whole coarse steps of {sample_name}, single-thread C oracle"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def max_over_ranks(ms, dist, torch, device):
+    """The slowest rank's time: every rank contributes its own and gets the max."""
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, cell_updates_per_step, steps, ms_total):
+    """Whole-job throughput of `world` independent replicas, timed by the slowest."""
+    return world * cell_updates_per_step * steps / (ms_total / 1000.0)
+
+
+def timed_steps(fb, torch, st, stream, warm, k):
+    """Mean device time (ms) of one step over k steps after `warm` untimed ones."""
+    fb.lts_advance(st, warm)
+    fb.synchronize(st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fb.lts_advance(st, k)
+    e1.record(stream)
+    fb.synchronize(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
 
 
 def main():
@@ -205,6 +240,8 @@ def main():
     ap.add_argument("--workload", default="basin")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other-precision and global FB-RK(3,2) comparison runs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -258,11 +295,9 @@ def main():
     ms_total = evs[0].elapsed_time(evs[-1])
     lat = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
     if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = max_over_ranks(ms_total, dist, torch, "cuda")
     ms_step = ms_total / args.steps
-    value = world * cu * args.steps / (ms_total / 1000.0)
+    value = replica_value(world, cu, args.steps, ms_total)
 
     # per-kernel profile (launch by launch with events on the same stream)
     prof = fb.state_profile_step(st)
@@ -313,6 +348,37 @@ def main():
                 "d2h_bytes_per_step": 8 * (nC + nE), "steps": n_e2e},
         "clocks": clk.summary(),
     }
+    if rank == 0 and world == 1 and not args.no_variants:
+        # the same workload in the other precision (fewer timed steps)
+        oprec = fb.FP64 if prec == fb.FP32_TENDENCY else fb.FP32_TENDENCY
+        ost = fb.state_init(mesh, fb.make_params(
+            s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd, rho0=fz.rho0,
+            rho_air=fz.rho_air, vortex=vt, precision=oprec, stream=stream.cuda_stream, use_graph=True),
+            s.h0, s.u0, s.bottom)
+        k2 = max(3, min(args.steps, 10))
+        oms = timed_steps(fb, torch, ost, stream, 3, k2)
+        line["other_precision"] = {"precision": "fp64" if oprec == fb.FP64 else "fp32",
+                                   "value": cu / (oms / 1000.0), "ms_per_step": oms, "steps": k2}
+        fb.state_destroy(ost)
+        # global FB-RK(3,2) at the finest level's step on the same mesh (no LTS):
+        # the time one coarse step's simulated interval takes without local time stepping
+        nl = int(info.nLevels)
+        if nl > 1:
+            ratio = int(np.prod(s.M))
+            gmesh = fb.mesh_create(s.mesh, s.fVertex, level=np.zeros(nC, np.int32), M=[])
+            gst = fb.state_init(gmesh, fb.make_params(
+                s.dt / ratio, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
+                rho0=fz.rho0, rho_air=fz.rho_air, vortex=vt, precision=prec, stream=stream.cuda_stream,
+                use_graph=True), s.h0, s.u0, s.bottom)
+            kg = ratio * max(2, min(args.steps // 20, 5))
+            gms = timed_steps(fb, torch, gst, stream, ratio, kg)
+            line["global_fbrk"] = {
+                "dt": s.dt / ratio, "steps": kg, "ms_per_step": gms,
+                "ms_per_coarse_interval": gms * ratio,
+                "cell_updates_per_s": nC / (gms / 1000.0),
+                "lts_speedup": gms * ratio / ms_step}
+            fb.state_destroy(gst)
+            fb.mesh_destroy(gmesh)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on a bounded sample: whole coarse steps of the workload, or of its
         # 1/8-length sample (same recipe) when one coarse step of the full mesh is too long
@@ -333,12 +399,16 @@ def main():
         wparams = fb.make_params(ws.dt, g=ws.g, forcing=forcing_flags(ws), wind=(wfz.wind_u, wfz.wind_v),
                                  cd=wfz.cd, rho0=wfz.rho0, rho_air=wfz.rho_air, vortex=wvt, precision=prec,
                                  stream=stream.cuda_stream, use_graph=True)
-        st2 = fb.state_init(wmesh, wparams, ws.h0, ws.u0, ws.bottom)
-        fb.lts_advance(st2, n)
-        h, u = fb.state_read(st2)
-        line["err_vs_oracle"] = {"workload": sample_name, "coarse_steps": n,
-                                 "h_rel_max": float(np.max(np.abs(h - ho) / np.abs(ho))),
-                                 "u_rel_max": float(np.max(np.abs(u - uo)) / max(np.max(np.abs(uo)), 1e-300))}
+        errs = {}
+        for pname, pv in (("fp32", fb.FP32_TENDENCY), ("fp64", fb.FP64)):
+            wparams.precision = pv
+            st2 = fb.state_init(wmesh, wparams, ws.h0, ws.u0, ws.bottom)
+            fb.lts_advance(st2, n)
+            h, u = fb.state_read(st2)
+            fb.state_destroy(st2)
+            errs[pname] = {"h_rel_max": float(np.max(np.abs(h - ho) / np.abs(ho))),
+                           "u_rel_max": float(np.max(np.abs(u - uo)) / max(np.max(np.abs(uo)), 1e-300))}
+        line["err_vs_oracle"] = {"workload": sample_name, "coarse_steps": n, **errs}
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -342,12 +342,12 @@ FB_HD float phi_from_shares(const DevMesh &m, const float *u_in, const DevForcin
     if (FORCING) {
         const float vt = idc * (h0.y + h1.y);
         const float ue = u_in[e];
-        const float he = m.He32[e] + 0.5f * (h0.w + h1.w);
+        const float rhe = 1.f / (m.He32[e] + 0.5f * (h0.w + h1.w));
         if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
             const float dn = fz.windN32[e] - ue, dt = fz.windT32[e] - vt;
-            phi += fz.cw32[e] * sqrtf(dn * dn + dt * dt) * dn / he;
+            phi += fz.cw32[e] * sqrtf(dn * dn + dt * dt) * dn * rhe;
         }
-        if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue / he;
+        if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue * rhe;
     }
     return phi;
 }
