@@ -121,10 +121,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# sources of the single-state kernels (their bodies, launches and tables)
+KERNEL_SOURCES = ("fblts_internal.h", "kernels.cuh", "kernel_bodies.cuh", "kernel_bodies32.cuh", "kernels.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2405_10505_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -231,6 +235,194 @@ def timed_steps(fb, torch, st, stream, warm, k):
     return e0.elapsed_time(e1) / k
 
 
+def run_ensemble(args, rank):
+    """Batched ensemble: `--members` shelf channels of seeded sizes (20k-800k
+    cells), vortex tracks and M in {2, 4, 8}, FP32-tendency.  Times rounds of
+    one coarse step of every member, first in the plain form (each member's
+    own captured step, one instance per launch, on its own stream), then as a
+    batch (fblts_batch_*, launch shape tuned online)."""
+    if rank != 0:
+        return
+    import torch
+    import paper_2405_10505_gb300 as fb
+    from synth import scenario
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    states, cells, cu, Ms = [], 0, 0, []
+    lo_c, hi_c = (int(x) for x in args.member_cells.split(","))
+    for i in range(args.members):
+        s = scenario.ensemble_member(i, n_min=lo_c, n_max=hi_c)
+        mesh = fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M)
+        fz = s.forcing
+        vt = list(fz.vortex) + [float(np.mean(s.fVertex))] if fz.vortex is not None else None
+        p = fb.make_params(s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
+                           rho0=fz.rho0, rho_air=fz.rho_air, vortex=vt, precision=fb.FP32_TENDENCY, use_graph=True)
+        states.append(fb.state_init(mesh, p, s.h0, s.u0, s.bottom))
+        cells += int(s.mesh.nCells)
+        cu += int(mesh.info().cell_updates_per_step)
+        Ms.append(int(s.M[0]))
+        del s
+    setup_s = time.time() - t0
+
+    def sync_all():
+        for st in states:
+            fb.synchronize(st)
+        torch.cuda.synchronize()
+
+    # plain: one member's captured coarse step per graph launch, members on their own streams
+    for _ in range(args.warmup):
+        for st in states:
+            fb.lts_advance(st, 1)
+    sync_all()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        for st in states:
+            fb.lts_advance(st, 1)
+    sync_all()
+    plain_s = time.perf_counter() - t
+    # batched: tuning rounds, warm-up, then timed rounds with events on the batch stream
+    stream = torch.cuda.Stream()
+    b = fb.batch_create(states, autotune=True, stream=stream.cuda_stream)
+    fb.batch_advance(b, 13)
+    fb.batch_advance(b, args.warmup)
+    fb.batch_synchronize(b)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for k in range(args.steps):
+            fb.batch_advance(b, 1)
+            evs[k + 1].record(stream)
+        fb.batch_synchronize(b)
+        torch.cuda.synchronize()
+    ms_total = evs[0].elapsed_time(evs[-1])
+    lat = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
+    info = fb.batch_info(b)
+    value = cu * args.steps / (ms_total / 1000.0)
+    plain = cu * args.steps / plain_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-tendency/f64-state", "data": "synthetic",
+        "config": {"workload": "ensemble", "members": args.members, "member_cells": [lo_c, hi_c], "cells": cells,
+                   "cell_updates_per_round": cu, "M": Ms,
+                   "description": "batched ensemble of periodic-in-y shelf channels of seeded sizes, "
+                                  "seeded roughness and Holland vortex track, M in {2,4,8}; one round = one "
+                                  "coarse step of every member", "parallelism": "single"},
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "plain": {"value": plain, "ms_per_round": 1000.0 * plain_s / args.steps,
+                  "launches_per_round": int(info.member_launches_per_round), "timing": "host clock, device synced"},
+        "batched_vs_plain": value / plain,
+        "batch": {"mode": ("merged launches", "graph branches", "merged per group, groups as branches",
+                           "merged per group of <= 4, groups as branches")[info.mode],
+                  "groups": info.groups,
+                  "launches_per_round": int(info.launches_per_round), "threads_per_block": info.threads_per_block,
+                  "ctas_per_sm": info.ctas_per_sm, "tile_order": "largest first" if info.tile_order == 0 else "member",
+                  "tuned": bool(info.tuned),
+                  "candidates_ms": {("branches" if k == 12 else "%s/tpb%d/cta%d" % (
+                      ("merged", "grouped", "grouped4")[k // 4], (128, 256)[(k // 2) % 2], (0, 8)[k % 2])):
+                      round(float(info.candidate_ms[k]), 3) for k in range(info.n_candidates)}},
+        "gpu_launches": int(info.launches_per_round * args.steps + args.members),
+        "setup_s": setup_s,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    fb.batch_destroy(b)
+
+
+def run_serve(args, rank):
+    """Serving loop: Poisson arrivals (rate --serve-rate per s, --serve-seconds
+    of arrivals) of storm-surge requests, each on the resident 512x512 shelf
+    channel or the 2.03M-cell basin (50/50), with a seeded vortex track and a
+    duration drawn from 1-48 simulated hours times --serve-hours-scale, under a
+    --serve-budget-gb HBM budget (fblts_server_*, FP32-tendency).  The same
+    request stream is also served one request at a time (the plain form)."""
+    if rank != 0:
+        return
+    import torch
+    import paper_2405_10505_gb300 as fb
+    from synth import scenario, basin
+    torch.cuda.set_device(0)
+    t_setup = time.time()
+    shelf = scenario.shelf_case(vortex=True)
+    bas = basin.basin_case()
+    kinds = []
+    for s in (shelf, bas):
+        mesh = fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M)
+        kinds.append((s, mesh, int(mesh.info().cell_updates_per_step)))
+    setup_s = time.time() - t_setup
+    rng = np.random.default_rng(2405)
+    reqs, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / args.serve_rate)
+        if t > args.serve_seconds:
+            break
+        k = int(rng.integers(0, 2))
+        s = kinds[k][0]
+        hours = float(rng.uniform(1.0, 48.0)) * args.serve_hours_scale
+        n = max(1, int(round(hours * 3600.0 / s.dt)))
+        v = list(s.forcing.vortex)
+        v[4] += float(rng.uniform(-0.1, 0.1)) * 1e6          # track origin and heading vary per request
+        v[5] += float(rng.uniform(-0.1, 0.1)) * 1e6
+        v[7] = float(rng.uniform(-2.0, 2.0))
+        reqs.append((t, k, n, v))
+
+    def serve(max_active):
+        srv = fb.server_create(hbm_budget=int(args.serve_budget_gb * 1e9), max_active=max_active,
+                               steps_per_issue=2)
+        ids, pending, done, failed = [], list(reqs), 0, []
+        t0 = time.perf_counter()
+        while done < len(reqs):
+            now = time.perf_counter() - t0
+            while pending and pending[0][0] <= now:
+                _, k, n, v = pending.pop(0)
+                s, mesh, _ = kinds[k]
+                fz = s.forcing
+                p = fb.make_params(s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
+                                   rho0=fz.rho0, rho_air=fz.rho_air, vortex=v + [float(np.mean(s.fVertex))],
+                                   precision=fb.FP32_TENDENCY)
+                ids.append((fb.server_submit(srv, mesh, p, s.h0, s.u0, s.bottom, n), k, n))
+            if fb.server_progress(srv):
+                for rid, _, _ in ids:
+                    status = fb.server_request_info(srv, rid).status
+                    if status in (fb.REQ_DONE, fb.REQ_FAILED):
+                        try:
+                            fb.server_take(srv, rid, read=True)
+                        except fb.FbltsError:
+                            failed.append(rid)
+                        done += 1
+            elif not pending and done < len(reqs):
+                time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        st = fb.server_stats(srv)
+        lat = sorted(fb.server_request_info(srv, rid).t_done - fb.server_request_info(srv, rid).t_submit
+                     for rid, _, _ in ids)
+        cu = sum(kinds[k][2] * n for _, k, n in ids)
+        fb.server_destroy(srv)
+        return {"value": cu / wall, "wall_s": wall, "requests": len(ids), "failed": len(failed),
+                "latency_s": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+                "max_running": int(st.max_running), "peak_device_gb": st.device_bytes_peak / 1e9}
+
+    with ClockSampler(0) as clk:
+        served = serve(0)
+    plain = serve(1)
+    line = {
+        "metric": METRIC, "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": served["requests"],
+        "warmup": 0, "ms_per_step": 1000.0 * served["wall_s"] / max(1, served["requests"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-tendency/f64-state", "data": "synthetic",
+        "config": {"workload": "serve", "rate_per_s": args.serve_rate, "arrival_window_s": args.serve_seconds,
+                   "hours_scale": args.serve_hours_scale, "budget_gb": args.serve_budget_gb,
+                   "meshes": ["shelf 512x512 (262k cells, M=4)", "basin (2.03M cells, 3 levels, M=8)"],
+                   "description": "Poisson arrivals of storm-surge requests, 50/50 on the two resident meshes, "
+                                  "seeded vortex tracks, durations U[1,48] simulated hours x hours_scale; "
+                                  "value = cell-updates/s over the run", "parallelism": "single"},
+        "served": served, "plain_one_at_a_time": plain, "served_vs_plain": served["value"] / plain["value"],
+        "latency_ms": {"p50": 1000.0 * served["latency_s"]["p50"], "p99": 1000.0 * served["latency_s"]["p99"]},
+        "setup_s": setup_s, "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -240,6 +432,14 @@ def main():
     ap.add_argument("--workload", default="basin")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--members", type=int, default=48, help="ensemble workload: members")
+    ap.add_argument("--member-cells", default="20000,800000",
+                    help="ensemble workload: range of member sizes (cells), lo,hi")
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="serve workload: arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="serve workload: arrival window (s)")
+    ap.add_argument("--serve-hours-scale", type=float, default=0.01,
+                    help="serve workload: factor on the 1-48 h durations")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="serve workload: HBM budget (GB)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other-precision and global FB-RK(3,2) comparison runs")
     args = ap.parse_args()
@@ -248,6 +448,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "ensemble" and args.impl != "reference":
+        run_ensemble(args, rank)
+        return
+    if args.workload == "serve" and args.impl != "reference":
+        run_serve(args, rank)
+        return
     s, desc = make_workload(args.workload)
     if args.impl == "reference":
         run_reference(args, s, desc, rank)

@@ -243,6 +243,10 @@ fblts_status fblts_state_save(const fblts_state *state, void *buf, size_t *len);
 /* Restores a checkpoint written by fblts_state_save for the same mesh. */
 fblts_status fblts_state_load(fblts_state *state, const void *buf, size_t len);
 
+/* Device bytes that fblts_state_init will allocate for one state on `mesh`
+ * in `precision` (one arena per state; host only, no device work). */
+fblts_status fblts_state_device_bytes(const fblts_mesh *mesh, int32_t precision, size_t *bytes);
+
 /* Launch statistics of one coarse step: kernels launched per step. */
 fblts_status fblts_state_launches_per_step(const fblts_state *state, int64_t *launches);
 
@@ -297,6 +301,130 @@ fblts_status fblts_state_step_bytes(const fblts_state *state, double *alg_bytes,
  */
 fblts_status fblts_diagnostics_static(const fblts_mesh *mesh, const double *d_h, const double *d_u,
                                       double *d_out, void *stream);
+
+/*
+ * Batched ensemble.  The paper advances one scenario at a time; a batch
+ * advances many independent states (members, each on its own mesh, with its
+ * own levels, M, forcing and dt) together.  fblts_batch_advance(b, n) leaves
+ * every member exactly as fblts_lts_advance(member, n) would, bitwise: the
+ * same per-element arithmetic runs, only the launches are shared.  One round
+ * (one coarse FB-LTS step, Sec. 2.2, of every member) is one CUDA graph in
+ * which each launch runs the next op of several members that share a kernel
+ * body, as a persistent grid over their tiles.
+ *
+ * Members: FP32-tendency states on meshes with cell rows (mesh_info flags
+ * bit 0), on the current device, each at most once; otherwise FBLTS_E_ARG.
+ * The batch borrows them: do not advance a member through
+ * fblts_lts_advance while the batch is in use, and destroy the batch before
+ * its members.  fblts_batch_advance orders itself after the members' pending
+ * work and their later calls after itself, so fblts_state_read and
+ * fblts_diagnostics on a member see the batch's result.
+ */
+typedef struct fblts_batch fblts_batch;
+
+typedef struct fblts_batch_opts {
+    /* 1: the first 13 rounds of fblts_batch_advance each run one candidate
+     * launch shape under CUDA events, then the fastest is kept: modes 0, 2, 3
+     * with threads per block 128 / 256 x CTAs per SM 0 / 8 (tiles largest
+     * first), then mode 1.  Those rounds advance the members like any
+     * other; they synchronise the host once each. */
+    int32_t autotune;
+    /* without autotune: */
+    int32_t threads_per_block; /* 128 or 256 (0 = 256) */
+    int32_t ctas_per_sm;       /* persistent grid = this x SM count CTAs looping over the tiles,
+                                * 1..32; 0 = one CTA per tile */
+    int32_t tile_order;        /* 0 largest member op first, 1 member order */
+    /* 0: all members merged into one chain of launches; 1: no merging, the
+     * members' own launches as parallel graph branches; 2: members with the
+     * same op sequence (levels and M) merged, each group a parallel branch;
+     * 3: as 2 with groups of at most 4 members */
+    int32_t mode;
+    void *stream;              /* cudaStream_t for the batch's work; NULL = a stream of its own */
+} fblts_batch_opts;
+
+typedef struct fblts_batch_info {
+    int32_t members, groups;                                   /* groups: distinct op sequences */
+    int32_t threads_per_block, ctas_per_sm, tile_order, mode; /* the shape in use */
+    int32_t tuned;                                             /* 1 once the shape is final */
+    int64_t launches_per_round;         /* batched launches per round */
+    int64_t member_launches_per_round;  /* what the members launch alone per coarse step */
+    int64_t cell_updates_per_round;     /* sum over the members */
+    int64_t rounds;                     /* rounds advanced so far */
+    /* tuning: the candidates in the order listed under autotune and each
+     * one's round time in ms (0 = not run) */
+    int32_t n_candidates;
+    float candidate_ms[16];
+} fblts_batch_info;
+
+fblts_status fblts_batch_create(fblts_state *const *members, int32_t n, const fblts_batch_opts *opts,
+                                fblts_batch **out);
+/* Advances every member by n coarse steps (asynchronous on the batch's stream,
+ * except for the tuning rounds). */
+fblts_status fblts_batch_advance(fblts_batch *batch, int64_t n);
+/* Waits for the batch and checks every member (FBLTS_E_UNSTABLE as for
+ * fblts_synchronize). */
+fblts_status fblts_batch_synchronize(fblts_batch *batch);
+fblts_status fblts_batch_get_info(const fblts_batch *batch, fblts_batch_info *info);
+fblts_status fblts_batch_destroy(fblts_batch *batch);
+
+/*
+ * Serving loop.  The paper runs one scenario; a server runs a stream of
+ * scenario requests.  Each request is an FB-LTS run (Sec. 2.2) of n_steps
+ * coarse steps on a resident mesh, and its result is bitwise what
+ * fblts_state_init + fblts_lts_advance(n_steps) + fblts_state_read give alone.
+ *
+ * Requests are admitted first come, first served while the device bytes of
+ * the running and finished-but-untaken states stay within hbm_budget (and
+ * at most max_active run).  Each admitted request gets its own state, stream
+ * and captured coarse step; the server issues steps_per_issue steps at a time
+ * on that stream, so the running requests' work overlaps on the GPU, and a
+ * request admitted while others run starts without waiting for them.
+ * fblts_server_progress does not block: call it in a loop.  The server
+ * borrows the meshes and the request's h0, u0, bottom until the request is
+ * admitted (request_info status leaves 0).
+ */
+typedef struct fblts_server fblts_server;
+
+typedef struct fblts_server_opts {
+    uint64_t hbm_budget;     /* bytes of request states on the device at once; 0 = no limit */
+    int32_t max_active;      /* running requests at once; 0 = no limit */
+    int32_t steps_per_issue; /* coarse steps issued per request per progress call; 0 = 1 */
+} fblts_server_opts;
+
+typedef struct fblts_request_desc {
+    const fblts_mesh *mesh;
+    fblts_params params;     /* as for fblts_state_init; stream must be NULL, use_graph is forced */
+    const double *h0, *u0, *bottom;   /* caller order, read at admission */
+    int64_t n_steps;         /* coarse steps to run */
+} fblts_request_desc;
+
+typedef struct fblts_request_info {
+    int32_t status;          /* 0 queued, 1 running, 2 done, 3 failed, 4 taken */
+    int32_t error;           /* fblts_status of a failed request */
+    int64_t steps_done, n_steps;
+    uint64_t device_bytes;   /* of its state */
+    double t_submit, t_admit, t_done;  /* seconds on the server's monotonic clock */
+} fblts_request_info;
+
+typedef struct fblts_server_stats {
+    int64_t queued, running, finished, max_running;
+    uint64_t device_bytes_in_use, device_bytes_peak;
+    int64_t cell_updates;    /* completed, over all requests */
+    double t_now;            /* seconds since fblts_server_create */
+} fblts_server_stats;
+
+fblts_status fblts_server_create(const fblts_server_opts *opts, fblts_server **out);
+/* Queues a request (FBLTS_E_OOM if it alone exceeds the budget); *id names it. */
+fblts_status fblts_server_submit(fblts_server *server, const fblts_request_desc *request, int64_t *id);
+/* Retires finished work, issues the next steps of the running requests and
+ * admits queued ones; *n_finished (may be NULL) = requests finished in this call. */
+fblts_status fblts_server_progress(fblts_server *server, int32_t *n_finished);
+fblts_status fblts_server_request_info(const fblts_server *server, int64_t id, fblts_request_info *info);
+/* Copies a finished request's h, u (caller order; either may be NULL) and
+ * frees its state; a failed request returns its error. */
+fblts_status fblts_server_take(fblts_server *server, int64_t id, double *h_out, double *u_out);
+fblts_status fblts_server_get_stats(const fblts_server *server, fblts_server_stats *stats);
+fblts_status fblts_server_destroy(fblts_server *server);
 
 #ifdef __cplusplus
 }

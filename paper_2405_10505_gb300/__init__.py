@@ -59,12 +59,52 @@ class FbltsError(RuntimeError):
         self.status = status
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("autotune", C.c_int32), ("threads_per_block", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("tile_order", C.c_int32), ("mode", C.c_int32), ("stream", C.c_void_p)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("members", C.c_int32), ("groups", C.c_int32), ("threads_per_block", C.c_int32),
+                ("ctas_per_sm", C.c_int32),
+                ("tile_order", C.c_int32), ("mode", C.c_int32), ("tuned", C.c_int32),
+                ("launches_per_round", C.c_int64),
+                ("member_launches_per_round", C.c_int64), ("cell_updates_per_round", C.c_int64),
+                ("rounds", C.c_int64), ("n_candidates", C.c_int32), ("candidate_ms", C.c_float * 16)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_uint64), ("max_active", C.c_int32), ("steps_per_issue", C.c_int32)]
+
+
+class RequestDesc(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("params", Params), ("h0", C.POINTER(C.c_double)),
+                ("u0", C.POINTER(C.c_double)), ("bottom", C.POINTER(C.c_double)), ("n_steps", C.c_int64)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("error", C.c_int32), ("steps_done", C.c_int64), ("n_steps", C.c_int64),
+                ("device_bytes", C.c_uint64), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("running", C.c_int64), ("finished", C.c_int64), ("max_running", C.c_int64),
+                ("device_bytes_in_use", C.c_uint64), ("device_bytes_peak", C.c_uint64),
+                ("cell_updates", C.c_int64), ("t_now", C.c_double)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_TAKEN = range(5)
+
 _LIB = None
 SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts_mesh_get_info",
            "fblts_state_init", "fblts_state_destroy", "fblts_lts_advance", "fblts_synchronize",
            "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
            "fblts_state_time", "fblts_state_save", "fblts_state_load", "fblts_state_launches_per_step",
-           "fblts_state_profile_step", "fblts_state_step_bytes", "fblts_diagnostics_static")
+           "fblts_state_profile_step", "fblts_state_step_bytes", "fblts_diagnostics_static",
+           "fblts_state_device_bytes", "fblts_batch_create", "fblts_batch_advance", "fblts_batch_synchronize", "fblts_batch_get_info",
+           "fblts_batch_destroy", "fblts_server_create", "fblts_server_submit", "fblts_server_progress",
+           "fblts_server_request_info", "fblts_server_take", "fblts_server_get_stats", "fblts_server_destroy")
 PROFILE_KINDS = ("cell", "vertex", "edge_prep", "edge", "save", "predict", "correct", "forcing", "step_end",
                  "trisk")
 
@@ -102,6 +142,19 @@ def lib():
             "fblts_state_profile_step": [V, _PD, C.POINTER(C.c_int64), _PD],
             "fblts_state_step_bytes": [V, _PD, C.POINTER(C.c_int64)],
             "fblts_diagnostics_static": [V, V, V, V, V],
+            "fblts_state_device_bytes": [V, C.c_int32, C.POINTER(C.c_size_t)],
+            "fblts_batch_create": [C.POINTER(V), C.c_int32, C.POINTER(BatchOpts), C.POINTER(V)],
+            "fblts_batch_advance": [V, C.c_int64],
+            "fblts_batch_synchronize": [V],
+            "fblts_batch_get_info": [V, C.POINTER(BatchInfo)],
+            "fblts_batch_destroy": [V],
+            "fblts_server_create": [C.POINTER(ServerOpts), C.POINTER(V)],
+            "fblts_server_submit": [V, C.POINTER(RequestDesc), C.POINTER(C.c_int64)],
+            "fblts_server_progress": [V, C.POINTER(C.c_int32)],
+            "fblts_server_request_info": [V, C.c_int64, C.POINTER(RequestInfo)],
+            "fblts_server_take": [V, C.c_int64, _PD, _PD],
+            "fblts_server_get_stats": [V, C.POINTER(ServerStats)],
+            "fblts_server_destroy": [V],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -309,6 +362,12 @@ def state_load(state, blob):
     _check(lib().fblts_state_load(state.handle, buf, len(blob)))
 
 
+def state_device_bytes(mesh, precision):
+    n = C.c_size_t()
+    _check(lib().fblts_state_device_bytes(mesh.handle, int(precision), C.byref(n)))
+    return n.value
+
+
 def launches_per_step(state):
     n = C.c_int64()
     _check(lib().fblts_state_launches_per_step(state.handle, C.byref(n)))
@@ -339,3 +398,123 @@ def diagnostics_static(mesh, d_h, d_u, d_out, stream=None):
     """
     _check(lib().fblts_diagnostics_static(mesh.handle, C.c_void_p(d_h), C.c_void_p(d_u), C.c_void_p(d_out),
                                           None if stream is None else C.c_void_p(stream)))
+
+
+class Batch:
+    """Handle of a batched ensemble; keeps its member states alive."""
+
+    def __init__(self, handle, members):
+        self.handle = handle
+        self.members = list(members)
+
+    def close(self):
+        if self.handle:
+            batch_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_create(states, autotune=True, threads_per_block=0, ctas_per_sm=0, tile_order=0, mode=0, stream=None):
+    """fblts_batch_create over FP32-tendency states on meshes with cell rows."""
+    arr = (C.c_void_p * len(states))(*[s.handle for s in states])
+    o = BatchOpts(int(bool(autotune)), int(threads_per_block), int(ctas_per_sm), int(tile_order), int(mode), stream)
+    h = C.c_void_p()
+    _check(lib().fblts_batch_create(arr, len(states), C.byref(o), C.byref(h)))
+    return Batch(h, states)
+
+
+def batch_advance(batch, n):
+    _check(lib().fblts_batch_advance(batch.handle, int(n)))
+
+
+def batch_synchronize(batch):
+    _check(lib().fblts_batch_synchronize(batch.handle))
+
+
+def batch_info(batch):
+    info = BatchInfo()
+    _check(lib().fblts_batch_get_info(batch.handle, C.byref(info)))
+    return info
+
+
+def batch_destroy(batch):
+    h, batch.handle = batch.handle, None
+    if h:
+        _check(lib().fblts_batch_destroy(h))
+
+
+class Server:
+    """Handle of a serving loop; keeps the submitted meshes and input arrays
+    alive until their requests are admitted."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self._inputs = {}
+
+    def close(self):
+        if self.handle:
+            server_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def server_create(hbm_budget=0, max_active=0, steps_per_issue=1):
+    o = ServerOpts(int(hbm_budget), int(max_active), int(steps_per_issue))
+    h = C.c_void_p()
+    _check(lib().fblts_server_create(C.byref(o), C.byref(h)))
+    return Server(h)
+
+
+def server_submit(server, mesh, params, h0, u0, bottom, n_steps):
+    """Queues a request; returns its id."""
+    h0, u0, bottom = _f64(h0), _f64(u0), _f64(bottom)
+    d = RequestDesc(mesh.handle, params, _p(h0, _PD), _p(u0, _PD), _p(bottom, _PD), int(n_steps))
+    rid = C.c_int64()
+    _check(lib().fblts_server_submit(server.handle, C.byref(d), C.byref(rid)))
+    server._inputs[rid.value] = (mesh, h0, u0, bottom)
+    return rid.value
+
+
+def server_progress(server):
+    n = C.c_int32()
+    _check(lib().fblts_server_progress(server.handle, C.byref(n)))
+    return n.value
+
+
+def server_request_info(server, rid):
+    info = RequestInfo()
+    _check(lib().fblts_server_request_info(server.handle, int(rid), C.byref(info)))
+    return info
+
+
+def server_take(server, rid, read=True):
+    """A finished request's (h, u) in caller order (None, None without read); frees its state."""
+    mesh = server._inputs[rid][0]
+    info = mesh.info()
+    h = np.empty(info.nCells) if read else None
+    u = np.empty(info.nEdges) if read else None
+    try:
+        _check(lib().fblts_server_take(server.handle, int(rid), _p(h, _PD), _p(u, _PD)))
+    finally:
+        server._inputs.pop(rid, None)
+    return h, u
+
+
+def server_stats(server):
+    s = ServerStats()
+    _check(lib().fblts_server_get_stats(server.handle, C.byref(s)))
+    return s
+
+
+def server_destroy(server):
+    h, server.handle = server.handle, None
+    if h:
+        _check(lib().fblts_server_destroy(h))

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfblts.so")
-SOURCES = ["mesh.cpp", "schedule.cpp", "kernels.cu", "api.cu", "static_diag.cu"]
+SOURCES = ["mesh.cpp", "schedule.cpp", "kernels.cu", "api.cu", "static_diag.cu", "batch.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

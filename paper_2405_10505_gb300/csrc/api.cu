@@ -3,9 +3,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
+#include "handles.h"
 #include "kernels.cuh"
 
 namespace fblts {
@@ -63,43 +65,6 @@ std::vector<T> slot_major(const std::vector<T> &v, int n, int k) {
 }  // namespace fblts
 
 using namespace fblts;
-
-#define CK(call)                                                                            \
-    do {                                                                                    \
-        cudaError_t err__ = (call);                                                         \
-        if (err__ != cudaSuccess) {                                                         \
-            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(err__), __FILE__,  \
-                      __LINE__);                                                            \
-            return err__ == cudaErrorMemoryAllocation ? FBLTS_E_OOM : FBLTS_E_CUDA;         \
-        }                                                                                   \
-    } while (0)
-
-struct fblts_mesh {
-    HostMesh hm;
-    int device = 0;
-    void *dbase = nullptr;
-    DevMesh dm{};
-    int *cell_n2o = nullptr, *cell_o2n = nullptr, *edge_n2o = nullptr, *edge_o2n = nullptr;
-};
-
-struct fblts_state {
-    const fblts_mesh *mesh = nullptr;
-    fblts_params p{};
-    cudaStream_t st = nullptr;
-    bool own_stream = false;
-    void *dbase = nullptr;
-    DevArrays arr{};
-    DevMesh dm{};
-    DevForcing fz{};
-    long long *d_step = nullptr;
-    int *d_flag = nullptr;
-    double *d_partials = nullptr, *d_diag = nullptr;
-    double *d_stage_c = nullptr, *d_stage_e = nullptr;
-    Schedule sched;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    int64_t steps = 0;
-};
 
 extern "C" const char *fblts_last_error(void) { return last_error_text(); }
 
@@ -318,8 +283,9 @@ extern "C" fblts_status fblts_state_destroy(fblts_state *s) {
     if (!s) return FBLTS_OK;
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     if (s->graph) cudaGraphDestroy(s->graph);
+    // stream-ordered release: no device-wide synchronisation (other states keep running)
+    if (s->dbase && s->st) cudaFreeAsync(s->dbase, s->st);
     if (s->st) cudaStreamSynchronize(s->st);
-    if (s->dbase) cudaFree(s->dbase);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
     return FBLTS_OK;
@@ -338,6 +304,75 @@ static fblts_status upload_state(fblts_state *s, const double *h, const double *
         CK(launch_zero_boundary(s->arr.a[A_U], s->dm.ebnd, nE, s->st));
     }
     if (s->arr.fp32 && (h || u)) CK(launch_fp32_shadows(s->dm, s->arr, s->st));
+    return FBLTS_OK;
+}
+
+// every device allocation of a state, in order; the sizing pass and the
+// carving pass of fblts_state_init walk the same list
+static std::vector<size_t> state_plan(const fblts_mesh *m, bool f32) {
+    const HostMesh &hm = m->hm;
+    const size_t nC = hm.nC, nE = hm.nE, nV = hm.nV;
+    auto is_double = [&](int a) {
+        return !f32 || a == A_H || a == A_U || a == A_ACCH || a == A_ACCU || a == A_SH0 || a == A_SU0;
+    };
+    auto count = [&](int a) -> size_t {
+        // FP32 path: the edge records {l F, q_e, l u, 0}, or with cell rows the
+        // two cells' 16-byte shares per edge
+        if (a == A_FQU) return (m->dm.rowS ? 8 : 4) * nE;
+        return arr_is_cell(a) ? nC : (arr_is_vert(a) ? nV : nE);
+    };
+    const size_t szc = sizeof(double) * nC, sze = sizeof(double) * nE;
+    std::vector<size_t> plan;
+    for (int a = 0; a < A_COUNT; ++a) plan.push_back(count(a) * (is_double(a) ? 8 : 4));
+    plan.push_back(szc);                                           // bottom
+    plan.push_back(sze); plan.push_back(sze); plan.push_back(sze); plan.push_back(szc);  // forcing (double)
+    if (f32) {
+        plan.push_back(4 * nC); plan.push_back(4 * nE);            // shadows
+        plan.push_back(4 * nC); plan.push_back(4 * nE); plan.push_back(4 * nV);  // depths
+        plan.push_back(16 * nE);                                   // per-edge record
+        plan.push_back(16 * nV);                                   // per-vertex record
+        plan.push_back(4 * nE); plan.push_back(4 * nE); plan.push_back(4 * nE);
+        plan.push_back(4 * nC);                                    // forcing (float)
+    }
+    plan.push_back(64);                                            // step counter + flag
+    plan.push_back(sizeof(double) * (2 * DIAG_BLOCKS + 2));        // diagnostics partials
+    plan.push_back(szc); plan.push_back(sze);                      // caller-order staging
+    return plan;
+}
+
+static size_t plan_bytes(const std::vector<size_t> &plan) {
+    Arena ar;
+    for (size_t b : plan) ar.reserve(b);
+    return ar.used + 256;
+}
+
+// The launch list of one coarse step with its algorithmic bytes.  States on
+// one mesh with the same step, coefficients, precision and forcing switches
+// share it: the mesh keeps the lists it has built.
+static void cached_schedule(const fblts_mesh *m, const fblts_params *p, Schedule &out) {
+    const bool f32 = p->precision == FBLTS_FP32_TENDENCY;
+    const bool trisk = f32 && m->dm.rowS != 0;
+    std::lock_guard<std::mutex> lock(m->cache_mu);
+    for (const auto &c : m->sched_cache)
+        if (c.dt == p->dt && c.beta[0] == p->beta[0] && c.beta[1] == p->beta[1] && c.beta[2] == p->beta[2] &&
+            c.f32 == f32 && c.forcing == p->forcing) {
+            out = c.sched;
+            return;
+        }
+    Schedule s;
+    build_schedule(m->hm, p->dt, p->beta, trisk, s);
+    schedule_bytes(m->hm, p->forcing, f32, s);
+    if (m->sched_cache.size() < 8) m->sched_cache.push_back({p->dt, {p->beta[0], p->beta[1], p->beta[2]}, f32, p->forcing, s});
+    out = std::move(s);
+}
+
+extern "C" fblts_status fblts_state_device_bytes(const fblts_mesh *m, int32_t precision, size_t *bytes) {
+    if (!m || !bytes) { set_error("state_device_bytes: NULL argument"); return FBLTS_E_ARG; }
+    if (precision != FBLTS_FP64 && precision != FBLTS_FP32_TENDENCY) {
+        set_error("state_device_bytes: unknown precision %d", precision);
+        return FBLTS_E_ARG;
+    }
+    *bytes = plan_bytes(state_plan(m, precision == FBLTS_FP32_TENDENCY));
     return FBLTS_OK;
 }
 
@@ -367,8 +402,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     if (!s) { set_error("state_init: host allocation failed"); return FBLTS_E_OOM; }
     s->mesh = m;
     s->p = *p;
-    const HostMesh &hm = m->hm;
-    const int nC = hm.nC, nE = hm.nE, nV = hm.nV;
+    const int nC = m->hm.nC;
     if (p->stream) {
         s->st = (cudaStream_t)p->stream;
     } else {
@@ -385,38 +419,16 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     auto is_double = [&](int a) {
         return !f32 || a == A_H || a == A_U || a == A_ACCH || a == A_ACCU || a == A_SH0 || a == A_SU0;
     };
-    auto count = [&](int a) -> size_t {
-        // FP32 path: the edge records {l F, q_e, l u, 0}, or with cell rows the
-        // two cells' 16-byte shares per edge
-        if (a == A_FQU) return (m->dm.rowS ? 8 : 4) * (size_t)nE;
-        return arr_is_cell(a) ? (size_t)nC : (arr_is_vert(a) ? (size_t)nV : (size_t)nE);
-    };
     // the launch list of one coarse step and its algorithmic bytes
-    build_schedule(hm, p->dt, p->beta, f32 && m->dm.rowS != 0, s->sched);
-    schedule_bytes(hm, p->forcing, f32, s->sched);
-    // every allocation in order; the sizing pass and the carving pass walk the same list
-    size_t szc = sizeof(double) * (size_t)nC, sze = sizeof(double) * (size_t)nE;
-    std::vector<size_t> plan;
-    for (int a = 0; a < A_COUNT; ++a) plan.push_back(count(a) * (is_double(a) ? 8 : 4));
-    plan.push_back(szc);                                           // bottom
-    plan.push_back(sze); plan.push_back(sze); plan.push_back(sze); plan.push_back(szc);  // forcing (double)
-    if (f32) {
-        plan.push_back(4 * (size_t)nC); plan.push_back(4 * (size_t)nE);            // shadows
-        plan.push_back(4 * (size_t)nC); plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nV);  // depths
-        plan.push_back(16 * (size_t)nE);                                            // per-edge record
-        plan.push_back(16 * (size_t)nV);                                            // per-vertex record
-        plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nE); plan.push_back(4 * (size_t)nE);
-        plan.push_back(4 * (size_t)nC);                                             // forcing (float)
-    }
-    plan.push_back(64);                                            // step counter + flag
-    plan.push_back(sizeof(double) * (2 * DIAG_BLOCKS + 2));        // diagnostics partials
-    plan.push_back(szc); plan.push_back(sze);                      // caller-order staging
+    cached_schedule(m, p, s->sched);
+    const std::vector<size_t> plan = state_plan(m, f32);
+    size_t szc = sizeof(double) * (size_t)nC;
     Arena ar;
-    for (size_t b : plan) ar.reserve(b);
-    ar.size = ar.used + 256;
-    if (cudaMalloc(&s->dbase, ar.size) != cudaSuccess) {
+    ar.size = plan_bytes(plan);
+    if (cudaMallocAsync(&s->dbase, ar.size, s->st) != cudaSuccess) {
         cudaGetLastError();
-        set_error("state_init: cudaMalloc of %zu bytes failed", ar.size);
+        s->dbase = nullptr;
+        set_error("state_init: device allocation of %zu bytes failed", ar.size);
         fblts_state_destroy(s);
         return FBLTS_E_OOM;
     }

@@ -249,3 +249,15 @@ def jittered_voronoi_case(k=38, L=300e3, jitter=0.45, H=1000.0, f=1e-4, amp=1.0,
     return Scenario(name=f"jittered_voronoi_{mesh.nCells}", mesh=mesh, bottom=np.full(mesh.nCells, -H),
                     fVertex=np.full(mesh.nVertices, f), h0=h0, u0=np.zeros(mesh.nEdges), level=level,
                     M=Ms, dt=float(dt), forcing=Forcing(wind_u=0.0, wind_v=0.0, cd=0.0, wind_stress=False))
+
+
+def ensemble_member(i, seed=2405, n_min=20_000, n_max=800_000):
+    """Member i of the batched ensemble: a shelf channel (``shelf_case``) of
+    seeded size N ~ U[n_min, n_max] cells (nx ~ sqrt(N), ny even), seeded
+    roughness and vortex track, M drawn from {2, 4, 8}."""
+    rng = _rng(seed + 7919 * (i + 1))
+    n = int(rng.integers(n_min, n_max + 1))
+    nx = max(16, int(round(np.sqrt(n))))
+    ny = max(4, 2 * int(round(n / nx / 2)))
+    M = int(rng.choice([2, 4, 8]))
+    return shelf_case(nx=nx, ny=ny, dc=2e3, M=M, seed=seed + i, vortex=True)

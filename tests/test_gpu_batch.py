@@ -1,0 +1,89 @@
+"""Batched ensemble (fblts_batch_*) against each member advanced alone.
+
+A batch shares launches between members but runs the same per-element
+arithmetic, so every member must come out bitwise equal to the same state
+advanced alone with fblts_lts_advance, for any launch shape and through the
+online tuning rounds.
+"""
+import numpy as np
+import pytest
+
+import paper_2405_10505_gb300 as fb
+from synth import scenario
+from tests.gpu_util import make_state
+
+pytestmark = pytest.mark.gpu
+
+
+def _members():
+    # uneven meshes: hex and irregular Voronoi cells (8- and 12-slot rows),
+    # 2 and 3 levels, M = 2 / 4, forcing off / wind + drag / vortex
+    return [
+        scenario.gaussian_bump_case(two_level=True),
+        scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3),
+        scenario.jittered_voronoi_case(),
+        scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3)),
+        scenario.shelf_case(nx=40, ny=32, dc=2e3, M=4, width=10e3, vortex=True),
+    ]
+
+
+def _alone(cases, n):
+    out = []
+    for s in cases:
+        st = make_state(s, precision=fb.FP32_TENDENCY)
+        fb.lts_advance(st, n)
+        out.append(fb.state_read(st))
+    return out
+
+
+@pytest.mark.parametrize("opts", [dict(autotune=True),
+                                  dict(autotune=False, threads_per_block=128, ctas_per_sm=2, tile_order=1),
+                                  dict(autotune=False, threads_per_block=256, ctas_per_sm=0, tile_order=0),
+                                  dict(autotune=False, mode=1),
+                                  dict(autotune=False, mode=2, threads_per_block=128, ctas_per_sm=8),
+                                  dict(autotune=False, mode=3)])
+def test_batch_equals_members_alone(opts):
+    cases = _members()
+    n = 15                                   # more rounds than the 13 tuning candidates
+    ref = _alone(cases, n)
+    states = [make_state(s, precision=fb.FP32_TENDENCY) for s in cases]
+    b = fb.batch_create(states, **opts)
+    fb.batch_advance(b, 4)
+    fb.batch_advance(b, n - 4)
+    fb.batch_synchronize(b)
+    info = fb.batch_info(b)
+    assert info.members == len(cases) and info.rounds == n
+    if info.mode == 0:
+        assert info.launches_per_round < info.member_launches_per_round
+    if opts["autotune"]:
+        assert info.tuned == 1
+    for st, (h0, u0) in zip(states, ref):
+        h, u = fb.state_read(st)
+        assert np.array_equal(h, h0) and np.array_equal(u, u0)
+    fb.batch_destroy(b)
+
+
+def test_batch_then_alone_continues_the_same_run():
+    cases = _members()[:3]
+    ref = _alone(cases, 6)
+    states = [make_state(s, precision=fb.FP32_TENDENCY) for s in cases]
+    b = fb.batch_create(states, autotune=False)
+    fb.batch_advance(b, 3)
+    fb.batch_destroy(b)
+    for st in states:
+        fb.lts_advance(st, 3)                 # the device step counter went on in the batch
+    for st, (h0, u0) in zip(states, ref):
+        h, u = fb.state_read(st)
+        assert np.array_equal(h, h0) and np.array_equal(u, u0)
+
+
+def test_batch_rejects_bad_members():
+    s = scenario.gaussian_bump_case(two_level=True)
+    st32 = make_state(s, precision=fb.FP32_TENDENCY)
+    st64 = make_state(s, precision=fb.FP64)
+    with pytest.raises(fb.FbltsError):
+        fb.batch_create([st32, st64])
+    with pytest.raises(fb.FbltsError):
+        fb.batch_create([st32, st32])
+    with pytest.raises(fb.FbltsError):
+        fb.batch_create([st32], autotune=False, threads_per_block=100)

@@ -1,0 +1,85 @@
+"""Serving loop (fblts_server_*) against each request run alone.
+
+Requests on different resident meshes, precisions and durations arrive
+while others run; admission is bounded by a device-byte budget.  Each result
+must be bitwise the state that fblts_state_init + fblts_lts_advance(n) +
+fblts_state_read give for the same request alone.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import paper_2405_10505_gb300 as fb
+from synth import scenario
+from tests.gpu_util import forcing_flags
+
+pytestmark = pytest.mark.gpu
+
+
+def _params(s, precision):
+    fz = s.forcing
+    vt = list(fz.vortex) + [float(np.mean(s.fVertex))] if fz.vortex is not None else None
+    return fb.make_params(s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
+                          rho0=fz.rho0, rho_air=fz.rho_air, vortex=vt, precision=precision)
+
+
+def _alone(mesh, s, precision, n):
+    st = fb.state_init(mesh, _params(s, precision), s.h0, s.u0, s.bottom)
+    fb.lts_advance(st, n)
+    out = fb.state_read(st)
+    fb.state_destroy(st)
+    return out
+
+
+def test_served_requests_equal_alone_runs():
+    cases = [scenario.gaussian_bump_case(two_level=True),
+             scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3, vortex=True),
+             scenario.jittered_voronoi_case()]
+    meshes = [fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M) for s in cases]
+    # (case, precision, steps): uneven durations, both precisions
+    reqs = [(0, fb.FP32_TENDENCY, 7), (1, fb.FP32_TENDENCY, 5), (2, fb.FP32_TENDENCY, 9),
+            (1, fb.FP64, 4), (0, fb.FP64, 6), (2, fb.FP32_TENDENCY, 3), (1, fb.FP32_TENDENCY, 8)]
+    sizes = [fb.state_device_bytes(meshes[c], p) for c, p, _ in reqs]
+    budget = int(2.5 * max(sizes))
+    srv = fb.server_create(hbm_budget=budget, steps_per_issue=2)
+    ids = []
+    for c, p, n in reqs[:4]:
+        ids.append(fb.server_submit(srv, meshes[c], _params(cases[c], p), cases[c].h0, cases[c].u0,
+                                    cases[c].bottom, n))
+    for _ in range(3):
+        fb.server_progress(srv)
+    for c, p, n in reqs[4:]:            # arrivals while others run
+        ids.append(fb.server_submit(srv, meshes[c], _params(cases[c], p), cases[c].h0, cases[c].u0,
+                                    cases[c].bottom, n))
+    results = {}
+    t0 = time.time()
+    while len(results) < len(ids):
+        assert time.time() - t0 < 120
+        fb.server_progress(srv)
+        st = fb.server_stats(srv)
+        assert st.device_bytes_in_use <= budget
+        for rid in ids:
+            if rid not in results and fb.server_request_info(srv, rid).status == fb.REQ_DONE:
+                results[rid] = fb.server_take(srv, rid)
+    st = fb.server_stats(srv)
+    assert st.finished == len(ids) and st.queued == 0 and st.running == 0
+    assert st.max_running >= 2 and st.device_bytes_peak <= budget
+    for rid, (c, p, n) in zip(ids, reqs):
+        info = fb.server_request_info(srv, rid)
+        assert info.status == fb.REQ_TAKEN and info.steps_done == n
+        assert info.t_submit <= info.t_admit <= info.t_done
+        h0, u0 = _alone(meshes[c], cases[c], p, n)
+        h, u = results[rid]
+        assert np.array_equal(h, h0) and np.array_equal(u, u0)
+    fb.server_destroy(srv)
+
+
+def test_server_rejects_what_can_never_fit():
+    s = scenario.gaussian_bump_case(two_level=True)
+    mesh = fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M)
+    need = fb.state_device_bytes(mesh, fb.FP32_TENDENCY)
+    srv = fb.server_create(hbm_budget=need - 1)
+    with pytest.raises(fb.FbltsError):
+        fb.server_submit(srv, mesh, _params(s, fb.FP32_TENDENCY), s.h0, s.u0, s.bottom, 3)
+    fb.server_destroy(srv)
