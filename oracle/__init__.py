@@ -55,7 +55,7 @@ class Params(C.Structure):
                 ("wind_stress", C.c_int), ("cd", C.c_double), ("rho0", C.c_double), ("rho_air", C.c_double),
                 ("vortex", C.c_int), ("vx_pc", C.c_double), ("vx_dp", C.c_double), ("vx_rmax", C.c_double),
                 ("vx_B", C.c_double), ("vx_x0", C.c_double), ("vx_y0", C.c_double), ("vx_vx", C.c_double),
-                ("vx_vy", C.c_double), ("vx_f0", C.c_double)]
+                ("vx_vy", C.c_double), ("vx_f0", C.c_double), ("split", C.c_int)]
 
 
 _lib = None
@@ -128,10 +128,11 @@ class Mesh:
         return cls(scn.mesh, scn.bottom, scn.fVertex)
 
 
-def params(g=GRAV, beta=BETA, terms=T_FULL, H_lin=0.0, forcing=None, f0=None):
-    """Oracle parameters; ``forcing`` is a ``synth.scenario.Forcing`` or None."""
+def params(g=GRAV, beta=BETA, terms=T_FULL, H_lin=0.0, forcing=None, f0=None, split=False):
+    """Oracle parameters; ``forcing`` is a ``synth.scenario.Forcing`` or None;
+    ``split`` selects the fast/slow operator splitting of Sec. 3.2."""
     p = Params(g, beta[0], beta[1], beta[2], terms, H_lin, 0.0, 0.0, 0, 0.0, 1025.0, 1.225,
-               0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+               0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, int(bool(split)))
     if forcing is not None and forcing.any:
         p.terms |= T_FORCING
         p.wind_u, p.wind_v = forcing.wind_u, forcing.wind_v
@@ -257,9 +258,9 @@ def regions(m, level, nIF1=2, nIF2=2):
     return cc, cd, ec, ed, st
 
 
-def scenario_params(scn, terms=T_FULL, beta=BETA):
+def scenario_params(scn, terms=T_FULL, beta=BETA, split=False):
     f0 = float(np.mean(scn.fVertex)) if scn.fVertex.size else 0.0
-    return params(g=scn.g, beta=beta, terms=terms, forcing=scn.forcing, f0=f0)
+    return params(g=scn.g, beta=beta, terms=terms, forcing=scn.forcing, f0=f0, split=split)
 
 
 def run_scenario(scn, nsteps, full_band=False, terms=T_FULL):

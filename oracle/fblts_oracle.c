@@ -78,6 +78,7 @@ typedef struct {
     double cd, rho0, rho_air;
     int vortex;
     double vx_pc, vx_dp, vx_rmax, vx_B, vx_x0, vx_y0, vx_vx, vx_vy, vx_f0;
+    int split;   /* 1: fast/slow operator splitting of Phi (Sec. 3.2) */
 } om_params;
 
 static const double OM_NAN = (double)NAN;
@@ -241,6 +242,41 @@ static double om_phi_edge(const om_mesh *m, const om_params *p, const om_forcing
     return val;
 }
 
+/* Operator splitting [Sec. 3.2, Eq. splitting, Eq. fast_terms].  With
+ * p->split, a Phi evaluation inside a coarse step is
+ *   Phi(u*, h*) ~ Phi_fast(u*, h*) + Phi_slow(u^n, h^n),
+ * Phi_fast = -g grad(h + b) (the external gravity-wave term) and Phi_slow the
+ * remaining terms (Coriolis, kinetic-energy gradient, forcing), evaluated once
+ * per coarse step from its start time level; Psi is not split.  `slow` holds
+ * Phi_slow per edge (NULL: no splitting). */
+static double om_phi_stage(const om_mesh *m, const om_params *p, const om_forcing *fz, const double *slow,
+                           const double *u, const double *h, const double *K, const double *q, int e) {
+    if (!slow) return om_phi_edge(m, p, fz, u, h, K, q, e);
+    om_params pf = *p;
+    pf.terms = p->terms & OM_T_PGRAD;
+    return om_phi_edge(m, &pf, NULL, u, h, K, q, e) + slow[e];
+}
+
+static void om_all_K(const om_mesh *m, const double *u, double *K);
+static void om_all_q(const om_mesh *m, const double *u, const double *h, double *q);
+
+/* Phi_slow(u, h) on every edge (0 on no-flow edges), or NULL without splitting. */
+static double *om_slow_terms(const om_mesh *m, const om_params *p, const om_forcing *fz, const double *u,
+                             const double *h) {
+    if (!p->split) return NULL;
+    om_params ps = *p;
+    ps.terms = p->terms & ~OM_T_PGRAD;
+    double *slow = (double *)malloc(sizeof(double) * (size_t)(m->nE > 0 ? m->nE : 1));
+    double *K = (double *)malloc(sizeof(double) * (size_t)(m->nC > 0 ? m->nC : 1));
+    double *q = (double *)malloc(sizeof(double) * (size_t)(m->nV > 0 ? m->nV : 1));
+    om_all_K(m, u, K);
+    om_all_q(m, u, h, q);
+    for (int e = 0; e < m->nE; ++e) slow[e] = om_phi_edge(m, &ps, fz, u, h, K, q, e);
+    free(K);
+    free(q);
+    return slow;
+}
+
 /* helpers computing K on all cells and q on all vertices (NaN where inputs are) */
 static void om_all_K(const om_mesh *m, const double *u, double *K) {
     for (int i = 0; i < m->nC; ++i) K[i] = om_ke_cell(m, u, i);
@@ -326,21 +362,23 @@ static void om_fbrk32_once(const om_mesh *m, const om_params *p, const om_forcin
     double *u1 = dalloc(nE), *u2 = dalloc(nE), *u3 = dalloc(nE);
     double *K = dalloc(nC), *q = dalloc(m->nV);
     const double b1 = p->beta1, b2 = p->beta2, b3 = p->beta3;
+    double *slow = om_slow_terms(m, p, fz, u, h);
     /* stage 1 */
     for (int i = 0; i < nC; ++i) h1[i] = h[i] + dt / 3.0 * om_psi_cell(m, p, u, h, i);
     for (int i = 0; i < nC; ++i) hs[i] = b1 * h1[i] + (1.0 - b1) * h[i];
     om_all_K(m, u, K); om_all_q(m, u, hs, q);
-    for (int e = 0; e < nE; ++e) u1[e] = u[e] + dt / 3.0 * om_phi_edge(m, p, fz, u, hs, K, q, e);
+    for (int e = 0; e < nE; ++e) u1[e] = u[e] + dt / 3.0 * om_phi_stage(m, p, fz, slow, u, hs, K, q, e);
     /* stage 2 */
     for (int i = 0; i < nC; ++i) h2[i] = h[i] + dt / 2.0 * om_psi_cell(m, p, u1, h1, i);
     for (int i = 0; i < nC; ++i) hs[i] = b2 * h2[i] + (1.0 - b2) * h[i];
     om_all_K(m, u1, K); om_all_q(m, u1, hs, q);
-    for (int e = 0; e < nE; ++e) u2[e] = u[e] + dt / 2.0 * om_phi_edge(m, p, fz, u1, hs, K, q, e);
+    for (int e = 0; e < nE; ++e) u2[e] = u[e] + dt / 2.0 * om_phi_stage(m, p, fz, slow, u1, hs, K, q, e);
     /* stage 3 */
     for (int i = 0; i < nC; ++i) h3[i] = h[i] + dt * om_psi_cell(m, p, u2, h2, i);
     for (int i = 0; i < nC; ++i) hs[i] = b3 * h3[i] + (1.0 - 2.0 * b3) * h2[i] + b3 * h[i];
     om_all_K(m, u2, K); om_all_q(m, u2, hs, q);
-    for (int e = 0; e < nE; ++e) u3[e] = u[e] + dt * om_phi_edge(m, p, fz, u2, hs, K, q, e);
+    for (int e = 0; e < nE; ++e) u3[e] = u[e] + dt * om_phi_stage(m, p, fz, slow, u2, hs, K, q, e);
+    free(slow);
     memcpy(h, h3, sizeof(double) * nC);
     memcpy(u, u3, sizeof(double) * nE);
     free(h1); free(h2); free(h3); free(hs); free(u1); free(u2); free(u3); free(K); free(q);
@@ -536,6 +574,7 @@ typedef struct {
     const int *M;
     int full_band; /* 1: compute every coarse sub-stage on all of F^5 (Sec. 3.3 simplification) */
     int status;
+    const double *slow; /* Phi_slow of the current coarse step (splitting), or NULL */
 } om_ctx;
 
 /* Interface prediction for one IF-1 value  [Eq. preds; Appendix A]:
@@ -585,7 +624,7 @@ static void stage_u(const om_ctx *c, const unsigned char *set, const double *bas
     om_all_q(m, u, hs, q);
     for (int e = 0; e < m->nE; ++e)
         if (set[e] && present2(m->cellsOnEdge + 2 * e))
-            out[e] = base[e] + cdt * om_phi_edge(m, c->p, c->fz, u, hs, K, q, e);
+            out[e] = base[e] + cdt * om_phi_stage(m, c->p, c->fz, c->slow, u, hs, K, q, e);
     free(K); free(q);
 }
 
@@ -783,7 +822,7 @@ static int om_fblts_region(om_ctx *c, int l, double tau, double *h, double *u, c
             om_all_q(m, Ub, Hs, q);
             for (int e = 0; e < nE; ++e)
                 if (eIF12[e] && present2(m->cellsOnEdge + 2 * e))
-                    accu[e] += om_phi_edge(m, p, c->fz, Ub, Hs, K, q, e);
+                    accu[e] += om_phi_stage(m, p, c->fz, c->slow, Ub, Hs, K, q, e);
             free(K); free(q); free(Ub); free(Hb); free(Hs);
         }
         for (int i = 0; i < nC; ++i) {
@@ -837,12 +876,16 @@ int om_fblts(const om_mesh *m, const om_params *p, const int *level, int L, cons
     int st = om_regions_build_internal(m, level, L, nIF1, nIF2, &r);
     if (st != OM_OK) { om_regions_free(&r); return st; }
     double *wn = dalloc(m->nE), *wt = dalloc(m->nE), *ps = dalloc(m->nC);
-    om_ctx c = {m, p, NULL, &r, M, full_band, OM_OK};
+    om_ctx c = {m, p, NULL, &r, M, full_band, OM_OK, NULL};
     om_forcing fz;
     for (int n = 0; n < nsteps && c.status == OM_OK; ++n) {
         om_make_forcing(m, p, t0 + n * dt, wn, wt, ps, &fz);
         c.fz = (p->terms & OM_T_FORCING) ? &fz : NULL;
+        double *slow = om_slow_terms(m, p, c.fz, u, h);
+        c.slow = slow;
         om_advance(&c, 0, dt, h, u, NULL, NULL, NULL, NULL);
+        free(slow);
+        c.slow = NULL;
     }
     free(wn); free(wt); free(ps);
     om_regions_free(&r);
