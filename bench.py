@@ -404,13 +404,14 @@ def run_serve(args, rank):
                 "max_running": int(st.max_running), "peak_device_gb": st.device_bytes_peak / 1e9}
 
     with ClockSampler(0) as clk:
-        served = serve(0)
+        served = serve(args.serve_max_active)
     plain = serve(1)
     line = {
         "metric": METRIC, "value": served["value"], "unit": UNIT, "n_gpus": 1, "steps": served["requests"],
         "warmup": 0, "ms_per_step": 1000.0 * served["wall_s"] / max(1, served["requests"]), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32-tendency/f64-state", "data": "synthetic",
         "config": {"workload": "serve", "rate_per_s": args.serve_rate, "arrival_window_s": args.serve_seconds,
+                   "max_active": args.serve_max_active,
                    "hours_scale": args.serve_hours_scale, "budget_gb": args.serve_budget_gb,
                    "meshes": ["shelf 512x512 (262k cells, M=4)", "basin (2.03M cells, 3 levels, M=8)"],
                    "description": "Poisson arrivals of storm-surge requests, 50/50 on the two resident meshes, "
@@ -440,6 +441,8 @@ def main():
     ap.add_argument("--serve-hours-scale", type=float, default=0.01,
                     help="serve workload: factor on the 1-48 h durations")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="serve workload: HBM budget (GB)")
+    ap.add_argument("--serve-max-active", type=int, default=0,
+                    help="serve workload: running requests at once (0 = as many as the budget allows)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other-precision and global FB-RK(3,2) comparison runs")
     args = ap.parse_args()
@@ -566,6 +569,16 @@ def main():
         line["other_precision"] = {"precision": "fp64" if oprec == fb.FP64 else "fp32",
                                    "value": cu / (oms / 1000.0), "ms_per_step": oms, "steps": k2}
         fb.state_destroy(ost)
+        # the fast/slow operator splitting of Sec. 3.2 (first order in time), same precision
+        sst = fb.state_init(mesh, fb.make_params(
+            s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd, rho0=fz.rho0,
+            rho_air=fz.rho_air, vortex=vt, precision=prec, stream=stream.cuda_stream, use_graph=True, split=True),
+            s.h0, s.u0, s.bottom)
+        sms = timed_steps(fb, torch, sst, stream, 3, max(3, min(args.steps, 20)))
+        sb, _ = fb.state_step_bytes(sst)
+        line["split"] = {"value": cu / (sms / 1000.0), "ms_per_step": sms, "speedup_vs_unsplit": ms_step / sms,
+                         "alg_bytes_per_step": sb, "step_hbm_frac": sb / (sms / 1000.0) / 1e9 / hbm}
+        fb.state_destroy(sst)
         # global FB-RK(3,2) at the finest level's step on the same mesh (no LTS):
         # the time one coarse step's simulated interval takes without local time stepping
         nl = int(info.nLevels)
@@ -614,6 +627,20 @@ def main():
             fb.state_destroy(st2)
             errs[pname] = {"h_rel_max": float(np.max(np.abs(h - ho) / np.abs(ho))),
                            "u_rel_max": float(np.max(np.abs(u - uo)) / max(np.max(np.abs(uo)), 1e-300))}
+        if not args.no_variants:
+            # the split FP32 path against the split oracle on the same window
+            import oracle as orc
+            hs_o, us_o = orc.fblts(orc.Mesh.from_scenario(ws), orc.scenario_params(ws, split=True), ws.level, ws.M,
+                                   ws.h0, ws.u0, ws.dt, n)
+            wparams.precision = fb.FP32_TENDENCY
+            wparams.split = 1
+            st2 = fb.state_init(wmesh, wparams, ws.h0, ws.u0, ws.bottom)
+            fb.lts_advance(st2, n)
+            h, u = fb.state_read(st2)
+            fb.state_destroy(st2)
+            errs["fp32_split"] = {"h_rel_max": float(np.max(np.abs(h - hs_o) / np.abs(hs_o))),
+                                  "u_rel_max": float(np.max(np.abs(u - us_o)) / max(np.max(np.abs(us_o)), 1e-300)),
+                                  "vs": "split oracle"}
         line["err_vs_oracle"] = {"workload": sample_name, "coarse_steps": n, **errs}
     if rank == 0:
         print(json.dumps(line))

@@ -183,6 +183,12 @@ enum {
  *  t0            time of the initial state (s).
  *  stream        cudaStream_t to issue work on, or NULL for an own stream.
  *  use_graph     non-zero: capture one coarse step as a CUDA graph.
+ *  split         non-zero: the fast/slow operator splitting of Sec. 3.2
+ *                (Eq. splitting): inside a coarse step Phi is replaced by the
+ *                pressure gradient -g grad(h + b) at the stage state plus the
+ *                remaining terms (Coriolis, kinetic-energy gradient, forcing)
+ *                evaluated once at the coarse step's start time level; Psi is
+ *                not split.  First order in time. 
  */
 typedef struct fblts_params {
     double g;
@@ -197,6 +203,7 @@ typedef struct fblts_params {
     double t0;
     void *stream;
     int32_t use_graph;
+    int32_t split;
 } fblts_params;
 
 /* Allocates the device state (one arena), uploads h0[nC], u0[nE] and the

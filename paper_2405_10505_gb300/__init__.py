@@ -50,7 +50,7 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("forcing", C.c_int32), ("wind_u", C.c_double),
                 ("wind_v", C.c_double), ("cd", C.c_double), ("rho0", C.c_double),
                 ("rho_air", C.c_double), ("vortex", C.c_double * 9), ("t0", C.c_double),
-                ("stream", C.c_void_p), ("use_graph", C.c_int32)]
+                ("stream", C.c_void_p), ("use_graph", C.c_int32), ("split", C.c_int32)]
 
 
 class FbltsError(RuntimeError):
@@ -280,7 +280,7 @@ def mesh_get_info(mesh):
 
 
 def make_params(dt, g=9.80616, beta=PAPER_BETA, precision=FP64, forcing=0, wind=(0.0, 0.0), cd=0.0,
-                rho0=1025.0, rho_air=1.225, vortex=None, t0=0.0, stream=None, use_graph=True):
+                rho0=1025.0, rho_air=1.225, vortex=None, t0=0.0, stream=None, use_graph=True, split=False):
     p = Params()
     p.g, p.dt = g, dt
     p.beta[:] = list(beta)
@@ -292,6 +292,7 @@ def make_params(dt, g=9.80616, beta=PAPER_BETA, precision=FP64, forcing=0, wind=
     p.t0 = t0
     p.stream = stream
     p.use_graph = int(bool(use_graph))
+    p.split = int(bool(split))
     return p
 
 

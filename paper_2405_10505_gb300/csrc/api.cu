@@ -353,16 +353,18 @@ static void cached_schedule(const fblts_mesh *m, const fblts_params *p, Schedule
     const bool f32 = p->precision == FBLTS_FP32_TENDENCY;
     const bool trisk = f32 && m->dm.rowS != 0;
     std::lock_guard<std::mutex> lock(m->cache_mu);
+    const bool split = p->split != 0;
     for (const auto &c : m->sched_cache)
         if (c.dt == p->dt && c.beta[0] == p->beta[0] && c.beta[1] == p->beta[1] && c.beta[2] == p->beta[2] &&
-            c.f32 == f32 && c.forcing == p->forcing) {
+            c.f32 == f32 && c.forcing == p->forcing && c.split == split) {
             out = c.sched;
             return;
         }
     Schedule s;
-    build_schedule(m->hm, p->dt, p->beta, trisk, s);
+    build_schedule(m->hm, p->dt, p->beta, trisk, split, s);
     schedule_bytes(m->hm, p->forcing, f32, s);
-    if (m->sched_cache.size() < 8) m->sched_cache.push_back({p->dt, {p->beta[0], p->beta[1], p->beta[2]}, f32, p->forcing, s});
+    if (m->sched_cache.size() < 8)
+        m->sched_cache.push_back({p->dt, {p->beta[0], p->beta[1], p->beta[2]}, f32, p->forcing, split, s});
     out = std::move(s);
 }
 

@@ -91,6 +91,7 @@ enum Arr : int {
     A_H = 0, A_U, A_HS1, A_HS2, A_HS3, A_HST1, A_HST2, A_HST3, A_US1, A_US2, A_US3,
     A_K, A_Q, A_FE, A_QE, A_FQ, A_FQU, A_ACCH, A_ACCU,
     A_SH0, A_SH1, A_SH2, A_SH3, A_SU0, A_SU1, A_SU2, A_SU3,
+    A_SLOW,   // per edge: the slow part of Phi at the coarse step's start (splitting)
     A_COUNT
 };
 bool arr_is_cell(int a);
@@ -103,7 +104,8 @@ enum SegMode : int {
     SEG_INPLACE = 2,  // overwrite the state array h / u (and FB average for cells)
     SEG_ACC_SET = 3,  // correction sum: acc = tendency
     SEG_ACC_ADD = 4,  // correction sum: acc += tendency
-    SEG_KONLY = 5     // cells: kinetic energy only
+    SEG_KONLY = 5,    // cells: kinetic energy only
+    SEG_PHI = 6       // edges: write the tendency itself (us_out = Phi)
 };
 
 struct Seg {
@@ -134,6 +136,9 @@ struct Op {
     int e_if1_lo = 0, e_if1_hi = 0, e_if12_hi = 0;
     int k = 0, Mk = 1;
     int level = 0;
+    // operator splitting (Sec. 3.2): 1 = this op evaluates the slow terms at
+    // the time level (no gravity term), 2 = edge stage with Phi = fast + slow
+    int split = 0;
     double alg_bytes = 0.0;           // algorithmic bytes of the launch (see op_bytes)
 };
 
@@ -145,7 +150,10 @@ struct Schedule {
 // trisk_cells: the Coriolis / tangential sums are formed per cell (OP_TRISK
 // over the cells of the edge pass) instead of per edge from edge records
 // (OP_EPREP over the edges and their neighbours)
-void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, Schedule &s);
+// split: the operator splitting of Sec. 3.2 (a slow-term evaluation at the
+// start of every coarse step, stages without the vertex / TRiSK passes)
+void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, bool split,
+                    Schedule &s);
 // fills Op::alg_bytes of every op (forcing: the edge passes read the forcing fields)
 void schedule_bytes(const HostMesh &hm, int forcing_flags, bool fp32, Schedule &s);
 

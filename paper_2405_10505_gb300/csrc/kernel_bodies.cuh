@@ -52,7 +52,9 @@ struct EdgeArgs {
     int lo, hi;
     const double *u_in, *hst, *K, *Fe, *qe, *FQ, *u0;
     double *us_out, *u_state, *acc;
+    const double *slow;   // splitting: the slow part of Phi per edge
     double cdt, g;
+    int split;            // 0, or 1: slow-term evaluation, 2: stage with Phi = fast + slow
 };
 
 struct IfArgs {
@@ -98,7 +100,9 @@ inline EdgeArgs edge_args(const Op &op, const DevArrays &arr, double g) {
     a.lo = op.lo; a.hi = op.hi;
     a.u_in = A[op.in_u]; a.hst = A[op.hst]; a.K = A[A_K]; a.Fe = A[A_FE]; a.qe = A[A_QE]; a.FQ = A[A_FQ];
     a.u0 = A[op.u0]; a.us_out = A[op.out_u]; a.u_state = A[A_U]; a.acc = A[A_ACCU];
+    a.slow = A[A_SLOW];
     a.cdt = op.cdt; a.g = g;
+    a.split = op.split;
     return a;
 }
 
@@ -195,7 +199,12 @@ FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, 
     const int mode = seg_mode(a.segs, e);
     if (mode == SEG_NONE) return;
     double phi = 0.0;
-    if (!m.ebnd[e]) {
+    if (!m.ebnd[e] && a.split == 2) {
+        // operator splitting [Sec. 3.2, Eq. splitting]: the gravity-wave term at the
+        // stage state plus the slow terms of the coarse step
+        const int c0 = m.coe0[e], c1 = m.coe1[e];
+        phi = a.slow[e] - a.g * ((a.hst[c1] + m.bottom[c1]) - (a.hst[c0] + m.bottom[c0])) * m.invDc[e];
+    } else if (!m.ebnd[e]) {
         const int nE = m.nE;
         const int c0 = m.coe0[e], c1 = m.coe1[e];
         const int n = m.nEoE[e];
@@ -210,7 +219,8 @@ FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, 
         }
         const double cor = 0.5 * (qself * sF + sG);
         const double h0c = a.hst[c0], h1c = a.hst[c1];
-        const double grad = (a.K[c1] - a.K[c0]) + a.g * ((h1c + m.bottom[c1]) - (h0c + m.bottom[c0]));
+        const double gg = a.split == 1 ? 0.0 : a.g;   // the slow terms leave gravity out
+        const double grad = (a.K[c1] - a.K[c0]) + gg * ((h1c + m.bottom[c1]) - (h0c + m.bottom[c0]));
         phi = cor - grad * m.invDc[e];
         if (FORCING) {
             const double ue = a.u_in[e];
@@ -228,6 +238,7 @@ FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, 
         case SEG_INPLACE: a.u_state[e] = m.ebnd[e] ? 0.0 : a.u_state[e] + a.cdt * phi; break;
         case SEG_ACC_SET: a.acc[e] = phi; break;
         case SEG_ACC_ADD: a.acc[e] += phi; break;
+        case SEG_PHI: a.us_out[e] = m.ebnd[e] ? 0.0 : phi; break;
         default: break;
     }
 }

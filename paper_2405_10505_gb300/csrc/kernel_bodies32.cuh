@@ -48,8 +48,10 @@ struct EdgeArgs32 {
     const float4 *half;
     float *us_out, *u_shadow;
     double *u_state, *acc;
+    const float *slow;   // splitting: the slow part of Phi per edge
     double cdt;
     float g;
+    int split;           // 0, or 1: slow-term evaluation, 2: stage with Phi = fast + slow
 };
 
 struct IfArgs32 {
@@ -83,27 +85,31 @@ inline CellArgs32 cell_args32(const Op &op, const DevArrays &arr, const DevMesh 
 }
 
 inline VertArgs32 vert_args32(const Op &op, const DevArrays &arr) {
-    return VertArgs32{op.lo, op.hi, f_in(arr, op.in_u), arr.f[op.hst], arr.f[A_Q]};
+    return VertArgs32{op.lo, op.hi, f_in(arr, op.in_u), f_in(arr, op.hst), arr.f[A_Q]};
 }
 
 inline PrepArgs32 prep_args32(const Op &op, const DevArrays &arr) {
-    return PrepArgs32{op.lo, op.hi, f_in(arr, op.in_u), arr.f[op.hst], arr.f[A_Q], (float4 *)arr.f[A_FQU]};
+    return PrepArgs32{op.lo, op.hi, f_in(arr, op.in_u), f_in(arr, op.hst), arr.f[A_Q], (float4 *)arr.f[A_FQU]};
 }
 
 inline TriskArgs32 trisk_args32(const Op &op, const DevArrays &arr, double g, double rho0) {
-    return TriskArgs32{op.lo, op.hi, f_in(arr, op.in_u), arr.f[op.hst], arr.f[A_K], arr.f[A_Q],
-                       (float4 *)arr.f[A_FQU], (float)g, (float)(rho0 > 0.0 ? 1.0 / rho0 : 0.0)};
+    // the slow-term evaluation of the splitting leaves the gravity term out of B
+    return TriskArgs32{op.lo, op.hi, f_in(arr, op.in_u), f_in(arr, op.hst), arr.f[A_K], arr.f[A_Q],
+                       (float4 *)arr.f[A_FQU], op.split == 1 ? 0.f : (float)g,
+                       (float)(rho0 > 0.0 ? 1.0 / rho0 : 0.0)};
 }
 
 inline EdgeArgs32 edge_args32(const Op &op, const DevArrays &arr, double g) {
     EdgeArgs32 a;
     a.segs = segs_of(op);
     a.lo = op.lo; a.hi = op.hi;
-    a.u_in = f_in(arr, op.in_u); a.hst = arr.f[op.hst]; a.K = arr.f[A_K]; a.fqu = (const float4 *)arr.f[A_FQU];
+    a.u_in = f_in(arr, op.in_u); a.hst = f_in(arr, op.hst); a.K = arr.f[A_K]; a.fqu = (const float4 *)arr.f[A_FQU];
     a.half = (const float4 *)arr.f[A_FQU];
     a.u0 = f_in(arr, op.u0); a.us_out = arr.f[op.out_u]; a.u_shadow = arr.u32;
     a.u_state = arr.a[A_U]; a.acc = arr.a[A_ACCU];
+    a.slow = arr.f[A_SLOW];
     a.cdt = op.cdt; a.g = (float)g;
+    a.split = op.split;
     return a;
 }
 
@@ -366,6 +372,7 @@ FB_HD void edge32_apply(const A &a, int mode, int e, bool bnd, float phi) {
         } break;
         case SEG_ACC_SET: a.acc[e] = (double)phi; break;
         case SEG_ACC_ADD: a.acc[e] += (double)phi; break;
+        case SEG_PHI: a.us_out[e] = bnd ? 0.f : phi; break;
         default: break;
     }
 }
@@ -381,7 +388,11 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
     if (mode == SEG_NONE) return;
     const bool bnd = m.ebnd[e] != 0;
     float phi = 0.f;
-    if (!bnd) {
+    if (!bnd && a.split == 2) {
+        // operator splitting [Sec. 3.2, Eq. splitting]: the gravity-wave term at the
+        // stage state plus the slow terms of the coarse step
+        phi = a.slow[e] - a.g * (a.hst[m.coe1[e]] - a.hst[m.coe0[e]]) * m.invDc32[e];
+    } else if (!bnd) {
         if constexpr (SHARES) {
             phi = phi_from_shares<FORCING>(m, a.u_in, fz, e, a.half[2 * e], a.half[2 * e + 1]);
         } else {
@@ -399,7 +410,7 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
                 if (FORCING) vt += w * r.z;
             }
             const float x0c = a.hst[c0], x1c = a.hst[c1];
-            const float grad = (a.K[c1] - a.K[c0]) + a.g * (x1c - x0c);
+            const float grad = (a.K[c1] - a.K[c0]) + (a.split == 1 ? 0.f : a.g) * (x1c - x0c);
             phi = cor - grad * idc;
             if (FORCING) {
                 const float ue = a.u_in[e];

@@ -38,8 +38,8 @@ struct AccInfo {
 
 class Builder {
 public:
-    Builder(const HostMesh &hm, const double beta[3], bool trisk_cells, Schedule &s)
-        : hm_(hm), s_(s), trisk_cells_(trisk_cells) {
+    Builder(const HostMesh &hm, const double beta[3], bool trisk_cells, bool split, Schedule &s)
+        : hm_(hm), s_(s), trisk_cells_(trisk_cells), split_(split) {
         b_[0] = beta[0]; b_[1] = beta[1]; b_[2] = beta[2];
     }
 
@@ -49,6 +49,7 @@ private:
     const HostMesh &hm_;
     Schedule &s_;
     bool trisk_cells_;
+    bool split_;
     double b_[3];
     std::map<std::pair<int, int>, std::array<int, 6>> memo_;
 
@@ -156,6 +157,16 @@ private:
         close_cells(c, clo, chi);
         s_.ops.push_back(c);
         if (ehi <= elo) return;
+        if (split_) {
+            // operator splitting: Phi = -g grad(h* + b) + the slow part of the step
+            Op e;
+            e.kind = OP_EDGE; e.stage = s; e.in_u = in_u; e.hst = hst; e.u0 = A_U; e.out_u = out_u; e.cdt = cdt;
+            e.split = 2;
+            for (auto &g : esegs) add_seg(e, g.begin, g.end, g.mode);
+            e.lo = elo; e.hi = ehi;
+            s_.ops.push_back(e);
+            return;
+        }
         // vertex pass
         Op v;
         v.kind = OP_VERT; v.stage = s; v.in_u = in_u; v.hst = hst; v.lo = vlo; v.hi = vhi;
@@ -348,6 +359,7 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
             }
             if (mode == SEG_ACC_SET) x = n * 8;
             if (mode == SEG_ACC_ADD) x = n * 16;
+            if (mode == SEG_PHI) x = n * R;
             return x;
         };
         switch (op.kind) {
@@ -390,6 +402,15 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
             } break;
             case OP_EDGE: {
                 if (all.empty()) break;
+                if (op.split == 2) {
+                    // splitting stage: ebnd, coe, 1/d_e, the slow part | the FB-averaged
+                    // thickness at the cells (+ bottom in double)
+                    const Touched &t = tch.get(OP_EPREP, all);
+                    b += t.self * (1 + 8 + C + R) + t.cells * (R + (fp32 ? 0 : 8));
+                    for (int k = 0; k < op.nseg; ++k)
+                        b += per_mode(op.seg[k].end - op.seg[k].begin, op.seg[k].mode, false);
+                    break;
+                }
                 if (fp32 && hm.rows_canonical) {
                     // ebnd, 1/d_e, the two cells' 16-byte shares
                     for (int k = 0; k < op.nseg; ++k) {
@@ -438,12 +459,35 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
     }
 }
 
-void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, Schedule &s) {
+void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, bool split,
+                    Schedule &s) {
     s.ops.clear();
     Op fz;
     fz.kind = OP_FORCING;
     s.ops.push_back(fz);
-    Builder b(hm, beta, trisk_cells, s);
+    if (split) {
+        // the slow part of Phi (Coriolis, kinetic-energy gradient, forcing) at
+        // the coarse step's start time level (h^n, u^n), on every edge
+        // [Sec. 3.2, Eq. splitting]
+        Op k;
+        k.kind = OP_CELL; k.stage = 1; k.in_u = A_U; k.in_h = A_H; k.hst = A_H; k.split = 1;
+        k.seg[0] = Seg{0, hm.nC, SEG_KONLY}; k.nseg = 1; k.lo = 0; k.hi = hm.nC;
+        s.ops.push_back(k);
+        Op v;
+        v.kind = OP_VERT; v.in_u = A_U; v.hst = A_H; v.split = 1;
+        v.seg[0] = Seg{0, hm.nV, SEG_UPD}; v.nseg = 1; v.lo = 0; v.hi = hm.nV;
+        s.ops.push_back(v);
+        Op p;
+        p.kind = trisk_cells ? OP_TRISK : OP_EPREP; p.in_u = A_U; p.hst = A_H; p.split = 1;
+        p.lo = 0; p.hi = trisk_cells ? hm.nC : hm.nE;
+        p.seg[0] = Seg{p.lo, p.hi, SEG_UPD}; p.nseg = 1;
+        s.ops.push_back(p);
+        Op e;
+        e.kind = OP_EDGE; e.in_u = A_U; e.hst = A_H; e.out_u = A_SLOW; e.split = 1;
+        e.seg[0] = Seg{0, hm.nE, SEG_PHI}; e.nseg = 1; e.lo = 0; e.hi = hm.nE;
+        s.ops.push_back(e);
+    }
+    Builder b(hm, beta, trisk_cells, split, s);
     b.top(dt);
     Op se;
     se.kind = OP_STEP_END;
