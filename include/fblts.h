@@ -313,8 +313,11 @@ fblts_status fblts_diagnostics_static(const fblts_mesh *mesh, const double *d_h,
  * Batched ensemble.  The paper advances one scenario at a time; a batch
  * advances many independent states (members, each on its own mesh, with its
  * own levels, M, forcing and dt) together.  fblts_batch_advance(b, n) leaves
- * every member exactly as fblts_lts_advance(member, n) would, bitwise: the
- * same per-element arithmetic runs, only the launches are shared.  One round
+ * every member as fblts_lts_advance(member, n) would: the same per-element
+ * arithmetic runs, only the launches are shared (bitwise in mode 1, which
+ * runs the members' own kernels; in the merged modes, whose kernels are
+ * compiled separately, float multiply-adds may be contracted differently, so
+ * results agree to the FP32 path's rounding).  One round
  * (one coarse FB-LTS step, Sec. 2.2, of every member) is one CUDA graph in
  * which each launch runs the next op of several members that share a kernel
  * body, as a persistent grid over their tiles.

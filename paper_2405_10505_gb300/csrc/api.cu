@@ -331,8 +331,7 @@ static std::vector<size_t> state_plan(const fblts_mesh *m, bool f32) {
         plan.push_back(4 * nC); plan.push_back(4 * nE); plan.push_back(4 * nV);  // depths
         plan.push_back(16 * nE);                                   // per-edge record
         plan.push_back(16 * nV);                                   // per-vertex record
-        plan.push_back(4 * nE); plan.push_back(4 * nE); plan.push_back(4 * nE);
-        plan.push_back(4 * nC);                                    // forcing (float)
+        plan.push_back(16 * nE); plan.push_back(4 * nC);           // forcing (float): per-edge record, p_s
     }
     plan.push_back(64);                                            // step counter + flag
     plan.push_back(sizeof(double) * (2 * DIAG_BLOCKS + 2));        // diagnostics partials
@@ -468,9 +467,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         Hv32 = (float *)got[gi++];
         estat = (float4 *)got[gi++];
         vkh = (float4 *)got[gi++];
-        s->fz.windN32 = (float *)got[gi++];
-        s->fz.windT32 = (float *)got[gi++];
-        s->fz.cw32 = (float *)got[gi++];
+        s->fz.wrec32 = (float4 *)got[gi++];
         s->fz.ps32 = (float *)got[gi++];
     }
     s->d_step = (long long *)got[gi++];

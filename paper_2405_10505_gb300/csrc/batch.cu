@@ -4,8 +4,10 @@
 // body (same pass, same template configuration) as a persistent grid over the
 // members' tiles.  Each tile copies its member's mesh tables, forcing and
 // launch arguments into shared memory and runs the same per-element bodies as
-// the single-state kernels, so a member's result is bitwise the same alone and
-// in any batch.  The launch shape (threads per block, resident CTAs per SM)
+// the single-state kernels, so a member's result is the same alone and in a
+// batch up to the float rounding of multiply-adds the compiler may contract
+// differently in these kernels (bitwise in branch mode, which launches the
+// members' own kernels).  The launch shape (threads per block, resident CTAs per SM)
 // and the order of the members' tiles are chosen online: the first rounds of
 // fblts_batch_advance each run one candidate shape under CUDA events, and the
 // fastest is kept.

@@ -30,6 +30,10 @@ struct PrepArgs32 {
     float4 *fqu;      // per edge {F_e, q_e, u_e, 0}
 };
 
+// row slots gathered unconditionally by the FP32 row kernels (hexagon-dominated
+// meshes); longer rows take a branch for the rest
+constexpr int ROW_MAIN = 6;
+
 // Cell-side TRiSK pass: per slot of each cell, the share {t, s_v, B_i, xi*_i}
 // of the cell in its edge's momentum tendency (trisk32_body), written to
 // half[2 e + side] (side 0 = first cell of e).
@@ -149,8 +153,8 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     int er[NMAX], nb[NMAX];
     float ue[NMAX], sdv[NMAX], kw[NMAX], He[NMAX];
     if constexpr (ROWS) {
-        // cell-major rows padded with valid indices: vector loads, then every
-        // gather unconditionally; the padding is masked
+        // cell-major rows padded with valid indices: vector loads, then the
+        // gathers of the first ROW_MAIN slots unconditionally (padding masked)
         static_assert(NMAX % 4 == 0, "row width");
         const int4 *e4 = reinterpret_cast<const int4 *>(m.rowE + (size_t)i * NMAX);
         const int4 *n4 = reinterpret_cast<const int4 *>(m.rowN + (size_t)i * NMAX);
@@ -162,13 +166,19 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
         }
         FB_UNROLL
         for (int j = 0; j < NMAX; ++j) {
-            const int e = er[j] < 0 ? ~er[j] : er[j];
-            const float u = a.u_in[e];
-            const float4 st = m.estat[e];
-            ue[j] = j < n ? u : 0.f;
-            kw[j] = st.y;
-            He[j] = st.z;
-            sdv[j] = j < n ? (er[j] < 0 ? st.x : -st.x) : 0.f;    // -n_{e,i} l_e
+            ue[j] = 0.f;
+            kw[j] = 0.f;
+            He[j] = 0.f;
+            sdv[j] = 0.f;
+            if (j < ROW_MAIN || n > ROW_MAIN) {   // slots past ROW_MAIN only for cells that have them
+                const int e = er[j] < 0 ? ~er[j] : er[j];
+                const float u = a.u_in[e];
+                const float4 st = m.estat[e];
+                ue[j] = j < n ? u : 0.f;
+                kw[j] = st.y;
+                He[j] = st.z;
+                sdv[j] = j < n ? (er[j] < 0 ? st.x : -st.x) : 0.f;    // -n_{e,i} l_e
+            }
         }
     } else {
         const int nC = m.nC;
@@ -206,7 +216,8 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     const float xi_i = a.xi_in[i];
     float F[NMAX];
     FB_UNROLL
-    for (int j = 0; j < NMAX; ++j) F[j] = (He[j] + 0.5f * (xi_i + a.xi_in[nb[j]])) * ue[j];
+    for (int j = 0; j < NMAX; ++j)
+        F[j] = (!ROWS || j < ROW_MAIN || n > ROW_MAIN) ? (He[j] + 0.5f * (xi_i + a.xi_in[nb[j]])) * ue[j] : 0.f;
     if (mode == SEG_UPD) {
         float S = 0.f;
         FB_UNROLL
@@ -214,7 +225,8 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
         const float x0 = a.xi0[i];
         const float xn = x0 + (float)a.cdt * (S * (float)invA);
         a.xi_out[i] = xn;
-        a.hst_out[i] = a.fb_a * xn + a.fb_b * a.xiprev[i] + a.fb_c * x0;
+        const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;   // the stage-2 value enters stage 3 only
+        a.hst_out[i] = a.fb_a * xn + a.fb_b * xp + a.fb_c * x0;
         return;
     }
     double S = 0.0;
@@ -228,7 +240,8 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
             const float xn = (float)(hn + a.bottom[i]);
             a.h_state[i] = hn;
             a.xi_shadow[i] = xn;
-            a.hst_out[i] = a.fb_a * xn + a.fb_b * a.xiprev[i] + a.fb_c * x0;
+            const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;   // the stage-2 value enters stage 3 only
+            a.hst_out[i] = a.fb_a * xn + a.fb_b * xp + a.fb_c * x0;
         } break;
         case SEG_ACC_SET: a.acc[i] = psi; break;
         case SEG_ACC_ADD: a.acc[i] += psi; break;
@@ -297,16 +310,23 @@ FB_HD void trisk32_body(const DevMesh &m, const TriskArgs32 &a, const DevForcing
     const float xs = a.hst[i];
     float B = a.K[i] + a.g * xs;
     if (VORTEX) B += fz.ps32[i] * a.inv_rho0;
+    // slots below ROW_MAIN gather unconditionally (padding reads valid entries
+    // and is masked); the rest only for the rare cells with more edges
     float lF[S], lu[S], qv[S];
     FB_UNROLL
     for (int j = 0; j < S; ++j) {
-        const int e = re[j] < 0 ? ~re[j] : re[j];
-        const float4 st = m.estat[e];
-        const float u = a.u_in[e];
-        const float xn = a.hst[rn[j]];
-        qv[j] = a.q[rv[j]];
-        lu[j] = j < n ? st.x * u : 0.f;
-        lF[j] = (st.z + 0.5f * (xs + xn)) * lu[j];
+        lu[j] = 0.f;
+        lF[j] = 0.f;
+        qv[j] = 0.f;
+        if (j < ROW_MAIN || n > ROW_MAIN) {
+            const int e = re[j] < 0 ? ~re[j] : re[j];
+            const float4 st = m.estat[e];
+            const float u = a.u_in[e];
+            const float xn = a.hst[rn[j]];
+            qv[j] = a.q[rv[j]];
+            lu[j] = j < n ? st.x * u : 0.f;
+            lF[j] = (st.z + 0.5f * (xs + xn)) * lu[j];
+        }
     }
     float qlast = qv[0];
     FB_UNROLL
@@ -348,10 +368,11 @@ FB_HD float phi_from_shares(const DevMesh &m, const float *u_in, const DevForcin
     if (FORCING) {
         const float vt = idc * (h0.y + h1.y);
         const float ue = u_in[e];
-        const float rhe = 1.f / (m.He32[e] + 0.5f * (h0.w + h1.w));
+        const float4 w = fz.wrec32[e];   // {wind normal, wind tangential, C_W, H_e}
+        const float rhe = 1.f / (w.w + 0.5f * (h0.w + h1.w));
         if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
-            const float dn = fz.windN32[e] - ue, dt = fz.windT32[e] - vt;
-            phi += fz.cw32[e] * sqrtf(dn * dn + dt * dt) * dn * rhe;
+            const float dn = w.x - ue, dt = w.y - vt;
+            phi += w.z * sqrtf(dn * dn + dt * dt) * dn * rhe;
         }
         if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue * rhe;
     }
@@ -414,10 +435,11 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
             phi = cor - grad * idc;
             if (FORCING) {
                 const float ue = a.u_in[e];
-                const float he = m.He32[e] + 0.5f * (x0c + x1c);
+                const float4 w = fz.wrec32[e];   // {wind normal, wind tangential, C_W, H_e}
+                const float he = w.w + 0.5f * (x0c + x1c);
                 if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
-                    const float dn = fz.windN32[e] - ue, dt = fz.windT32[e] - vt;
-                    phi += fz.cw32[e] * sqrtf(dn * dn + dt * dt) * dn / he;
+                    const float dn = w.x - ue, dt = w.y - vt;
+                    phi += w.z * sqrtf(dn * dn + dt * dt) * dn / he;
                 }
                 if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue / he;
                 if (fz.flags & FBLTS_FORCE_VORTEX) phi -= (fz.ps32[c1] - fz.ps32[c0]) * idc / (float)fz.rho0;
@@ -518,9 +540,8 @@ FB_HD void forcing32_body(const DevMesh &m, const DevForcing &fz, double time, i
         }
         const float c = (float)m.cosE[t], s = (float)m.sinE[t];
         const float wn = wu * c + wv * s, wt = -wu * s + wv * c;
-        fz.windN32[t] = wn;
-        fz.windT32[t] = wt;
-        fz.cw32[t] = (float)(fz.rho_air / fz.rho0) * (0.75f + 0.067f * sqrtf(wn * wn + wt * wt)) * 1e-3f;
+        const float cw = (float)(fz.rho_air / fz.rho0) * (0.75f + 0.067f * sqrtf(wn * wn + wt * wt)) * 1e-3f;
+        fz.wrec32[t] = make_float4(wn, wt, cw, m.He32[t]);
     }
     if (t < m.nC) {
         float a, b;

