@@ -139,8 +139,6 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     addd(slot_major(hm.cKite, nV, 3), &dm.cKite);
     addd(hm.fV, &dm.fV);
     addd(hm.Av, &dm.Av);
-    addf(slot_major(hm.cDiv, nC, mE), &dm.cDiv32);
-    addf(slot_major(hm.cKE, nC, mE), &dm.cKE32);
     {   // FP32 list weights W_{e,e'} / l_{e'}: the edge records carry l_{e'}
         std::vector<double> w(hm.woe);
         for (int e = 0; e < nE; ++e)
@@ -151,9 +149,6 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
         addf(slot_major(w, nE, mE2), &dm.woe32);
     }
     addf(hm.invDc, &dm.invDc32);
-    addf(slot_major(hm.cVort, nV, 3), &dm.cVort32);
-    addf(slot_major(hm.cKite, nV, 3), &dm.cKite32);
-    addf(hm.fV, &dm.fV32);
     {   // FP32 vertex pass: {e0, e1, e2, c0}, {c1, c2}, {t d / A_v x3, f} per vertex
         std::vector<int> i4((size_t)nV * 4), i2((size_t)nV * 2);
         std::vector<double> f4((size_t)nV * 4);
@@ -328,7 +323,7 @@ static std::vector<size_t> state_plan(const fblts_mesh *m, bool f32) {
     plan.push_back(sze); plan.push_back(sze); plan.push_back(sze); plan.push_back(szc);  // forcing (double)
     if (f32) {
         plan.push_back(4 * nC); plan.push_back(4 * nE);            // shadows
-        plan.push_back(4 * nC); plan.push_back(4 * nE); plan.push_back(4 * nV);  // depths
+        plan.push_back(4 * nE);                                    // H_e
         plan.push_back(16 * nE);                                   // per-edge record
         plan.push_back(16 * nV);                                   // per-vertex record
         plan.push_back(16 * nE); plan.push_back(4 * nC);           // forcing (float): per-edge record, p_s
@@ -457,14 +452,12 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     s->fz.windT = (double *)got[gi++];
     s->fz.cw = (double *)got[gi++];
     s->fz.ps = (double *)got[gi++];
-    float *H32 = nullptr, *He32 = nullptr, *Hv32 = nullptr;
+    float *He32 = nullptr;
     float4 *estat = nullptr, *vkh = nullptr;
     if (f32) {
         s->arr.xi32 = (float *)got[gi++];
         s->arr.u32 = (float *)got[gi++];
-        H32 = (float *)got[gi++];
         He32 = (float *)got[gi++];
-        Hv32 = (float *)got[gi++];
         estat = (float4 *)got[gi++];
         vkh = (float4 *)got[gi++];
         s->fz.wrec32 = (float4 *)got[gi++];
@@ -492,8 +485,8 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         }
     }
     if (st == FBLTS_OK && f32) {
-        s->dm.H32 = H32; s->dm.He32 = He32; s->dm.Hv32 = Hv32; s->dm.estat = estat; s->dm.vKh = vkh;
-        if (launch_fp32_depths(s->dm, H32, He32, Hv32, estat, vkh, s->st) != cudaSuccess ||
+        s->dm.He32 = He32; s->dm.estat = estat; s->dm.vKh = vkh;
+        if (launch_fp32_depths(s->dm, He32, estat, vkh, s->st) != cudaSuccess ||
             launch_fp32_shadows(s->dm, s->arr, s->st) != cudaSuccess) {
             set_error("state_init: FP32 setup failed");
             st = FBLTS_E_CUDA;

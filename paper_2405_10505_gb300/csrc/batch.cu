@@ -33,7 +33,7 @@ enum BodyKind : int {
 };
 
 // one member's op in a batched launch
-struct BatchItem {
+struct alignas(16) BatchItem {
     DevMesh m;
     DevForcing fz;
     union Args {
@@ -48,7 +48,6 @@ struct BatchItem {
     int lo;            // first element (cells, vertices, edges) or 0 for the interface ops
     int n;             // threads of work
     int tile0;         // first tile of the item in its launch
-    int pad[3];
 };
 static_assert(sizeof(BatchItem) % 16 == 0, "item copied as int4");
 

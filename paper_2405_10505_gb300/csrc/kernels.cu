@@ -132,12 +132,11 @@ __global__ void __launch_bounds__(TPB) forcing32_pass(DevMesh m, DevForcing fz) 
     forcing32_body(m, fz, time, t);
 }
 
-// resting depth seen by the FP32 path: H per cell, mean over the present cells
-// of an edge (also in the per-edge record {l_e, d_e l_e / 4, H_e, 0}),
-// kite-weighted mean at a vertex
-__global__ void fp32_depths(DevMesh m, float *H32, float *He32, float *Hv32, float4 *estat, float4 *vkh) {
+// resting depth seen by the FP32 path: H_e, the mean over the two cells of an
+// edge (also in the per-edge record {l_e, d_e l_e / 4, H_e, 0}), and the
+// per-vertex record {kite / A_v x3, H_v} with the kite-weighted mean H_v
+__global__ void fp32_depths(DevMesh m, float *He32, float4 *estat, float4 *vkh) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < m.nC) H32[t] = (float)(-m.bottom[t]);
     if (t < m.nE) {
         const float He = (float)(-0.5 * (m.bottom[m.coe0[t]] + m.bottom[m.coe1[t]]));
         He32[t] = He;
@@ -146,7 +145,6 @@ __global__ void fp32_depths(DevMesh m, float *H32, float *He32, float *Hv32, flo
     if (t < m.nV) {
         double s = 0.0;
         for (int j = 0; j < 3; ++j) s += m.cKite[j * m.nV + t] * (-m.bottom[m.cov[j * m.nV + t]]);
-        Hv32[t] = (float)s;
         vkh[t] = make_float4((float)m.cKite[t], (float)m.cKite[m.nV + t], (float)m.cKite[2 * m.nV + t], (float)s);
     }
 }
@@ -325,10 +323,10 @@ static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &
     return cudaGetLastError();
 }
 
-cudaError_t launch_fp32_depths(const DevMesh &m, float *H32, float *He32, float *Hv32, float4 *estat,
+cudaError_t launch_fp32_depths(const DevMesh &m, float *He32, float4 *estat,
                                float4 *vkh, cudaStream_t st) {
     const int n = m.nE > m.nV ? (m.nE > m.nC ? m.nE : m.nC) : (m.nV > m.nC ? m.nV : m.nC);
-    fp32_depths<<<nblk(n), TPB, 0, st>>>(m, H32, He32, Hv32, estat, vkh);
+    fp32_depths<<<nblk(n), TPB, 0, st>>>(m, He32, estat, vkh);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ struct DevMesh {
     const int *eov, *cov;               // vertices
     const double *cVort, *cKite, *fV, *Av;
     // single-precision copies of the coefficients (FP32-tendency path)
-    const float *cDiv32, *cKE32, *woe32, *invDc32, *cVort32, *cKite32, *fV32;
+    const float *woe32, *invDc32;
     // neighbour edges from the cells' edge rows: slots and weights in row order (FP32 path)
     const int *eocS;                    // edge rows with the sign n_{e,i} (~e for the second cell)
     const float *dv32, *ke32;           // l_e and d_e l_e / 4 per edge
@@ -42,7 +42,7 @@ struct DevMesh {
     const float *rowP;                  // [nC * rowS] prefix sums of the kite fractions
     const int *rowN, *rowV;             // [nC * rowS] neighbour cell / counter-clockwise vertex per slot
     // resting depth H = -b as seen by the FP32 path: per cell, edge mean, vertex mean (per state)
-    const float *H32, *He32, *Hv32;
+    const float *He32;
 };
 
 struct DevForcing {
@@ -83,7 +83,7 @@ cudaError_t launch_op(const Op &op, const DevMesh &m, const DevArrays &arr, cons
 
 // FP32-tendency path: resting depths seen by the float kernels, and the
 // float shadows of the double time level (after any write of h, u)
-cudaError_t launch_fp32_depths(const DevMesh &m, float *H32, float *He32, float *Hv32, float4 *estat,
+cudaError_t launch_fp32_depths(const DevMesh &m, float *He32, float4 *estat,
                                float4 *vkh, cudaStream_t st);
 cudaError_t launch_fp32_shadows(const DevMesh &m, const DevArrays &arr, cudaStream_t st);
 
