@@ -49,6 +49,10 @@ def make_workload(name):
         from synth import basin
         s = basin.basin_case(Ly=1200e3)
         desc = "1/8-length sample of the basin workload (same recipe, Ly 1200 km, ~0.25M cells)"
+    elif name == "basin_tiny":
+        from synth import basin
+        s = basin.basin_case(Ly=150e3)
+        desc = "1/64-length sample of the basin workload (same recipe, Ly 150 km, ~32k cells)"
     elif name == "bump":
         s = scenario.gaussian_bump_case(two_level=True)
         desc = "doubly periodic 32x32 hex, flat 1000 m, Gaussian bump, 2 LTS levels (M=2)"
@@ -180,10 +184,11 @@ def cell_updates_per_step(s):
 
 def reference_sample(workload, s):
     """The workload the oracle times per step: the workload itself, or for the
-    2M-cell basin (about 100 s per oracle coarse step) its 1/8-length sample."""
+    2M-cell basin (about 100 s per oracle coarse step) its 1/64-length sample
+    (about 1.5 s per step, so a run of ~100 steps ends within a few minutes)."""
     if workload == "basin":
-        ws, _ = make_workload("basin_small")
-        return ws, "basin_small (1/8-length sample of the basin: same recipe, Ly 1200 km)"
+        ws, _ = make_workload("basin_tiny")
+        return ws, "basin_tiny (1/64-length sample of the basin: same recipe, Ly 150 km, 31.7k cells)"
     return s, workload
 
 
