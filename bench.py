@@ -182,6 +182,35 @@ def cell_updates_per_step(s):
     return cu
 
 
+# classical RK4 is stable on the imaginary axis up to |omega dt| = 2 sqrt(2)
+RK4_IMAG_LIMIT = 2.0 * np.sqrt(2.0)
+
+
+def fbrk32_imag_limit(beta):
+    """Largest omega*dt for which one FB-RK(3,2) step (Eq. fbrk32, FB weights
+    beta) of the oscillator h' = u, u' = -h does not amplify: the linear
+    gravity-wave limit, used to put RK4 at the same fraction of its own limit."""
+    b1, b2, b3 = beta
+
+    def step(h, u, t):
+        h1 = h + t / 3 * u
+        u1 = u - t / 3 * (b1 * h1 + (1 - b1) * h)
+        h2 = h + t / 2 * u1
+        u2 = u - t / 2 * (b2 * h2 + (1 - b2) * h)
+        h3 = h + t * u2
+        u3 = u - t * (b3 * h3 + (1 - 2 * b3) * h2 + b3 * h)
+        return h3, u3
+
+    def rho(t):
+        return max(abs(np.linalg.eigvals(np.array([step(1.0, 0.0, t), step(0.0, 1.0, t)]).T)))
+
+    lo, hi = 0.5, 6.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if rho(mid) <= 1 + 1e-12 else (lo, mid)
+    return lo
+
+
 def reference_sample(workload, s):
     """The workload the oracle times per step: the workload itself, or for the
     2M-cell basin (about 100 s per oracle coarse step) its 1/64-length sample
@@ -602,6 +631,25 @@ def main():
                 "cell_updates_per_s": nC / (gms / 1000.0),
                 "lts_speedup": gms * ratio / ms_step}
             fb.state_destroy(gst)
+            # classical RK4 (the paper's comparison integrator, Sec. 4.2, Tab. 2) on the
+            # same one-level mesh, at the finest step scaled by the ratio of the two
+            # schemes' linear gravity-wave stability limits
+            rk_ratio = RK4_IMAG_LIMIT / fbrk32_imag_limit(fb.PAPER_BETA)
+            dt_rk = s.dt / ratio * rk_ratio
+            rst = fb.state_init(gmesh, fb.make_params(
+                dt_rk, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
+                rho0=fz.rho0, rho_air=fz.rho_air, vortex=vt, precision=prec, stream=stream.cuda_stream,
+                use_graph=True, scheme=fb.SCHEME_RK4), s.h0, s.u0, s.bottom)
+            kr = max(10, min(args.steps, 50))
+            rms = timed_steps(fb, torch, rst, stream, 3, kr)
+            per_interval = rms * s.dt / dt_rk
+            rb, _ = fb.state_step_bytes(rst)
+            line["global_rk4"] = {
+                "dt": dt_rk, "dt_over_fbrk32_dt": rk_ratio, "steps": kr, "ms_per_step": rms,
+                "ms_per_coarse_interval": per_interval, "cell_updates_per_s": nC / (rms / 1000.0),
+                "step_hbm_frac": rb / (rms / 1000.0) / 1e9 / hbm,
+                "lts_speedup": per_interval / ms_step, "split_lts_speedup": per_interval / sms}
+            fb.state_destroy(rst)
             fb.mesh_destroy(gmesh)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on a bounded sample: whole coarse steps of the workload, or of its

@@ -156,6 +156,7 @@ fblts_status fblts_mesh_get_info(const fblts_mesh *mesh, fblts_mesh_info *info);
 /* ---------------------------------------------------------------------- */
 
 enum { FBLTS_FP64 = 0, FBLTS_FP32_TENDENCY = 1 };
+enum { FBLTS_SCHEME_FBLTS = 0, FBLTS_SCHEME_RK4 = 1 };
 enum {
     FBLTS_FORCE_WIND_STRESS = 1, /* C_W |u_W - u| (u_W - u) / h, Eq. hurricane_model */
     FBLTS_FORCE_BOTTOM_DRAG = 2, /* -C_D |u| u / h */
@@ -188,7 +189,14 @@ enum {
  *                pressure gradient -g grad(h + b) at the stage state plus the
  *                remaining terms (Coriolis, kinetic-energy gradient, forcing)
  *                evaluated once at the coarse step's start time level; Psi is
- *                not split.  First order in time. 
+ *                not split.  First order in time.
+ *  scheme        FBLTS_SCHEME_FBLTS (0): FB-LTS (Sec. 2.2; on a one-level mesh
+ *                global FB-RK(3,2), Eq. fbrk32).  FBLTS_SCHEME_RK4 (1): the
+ *                classical four-stage Runge-Kutta scheme, the paper's
+ *                comparison integrator (Sec. 4.2, Tab. 2), advancing the unsplit
+ *                tendencies of all cells with dt; it needs a one-level mesh
+ *                and split = 0 (else FBLTS_E_ARG).  Wind and pressure are
+ *                evaluated at the start of each step and held for its stages.
  */
 typedef struct fblts_params {
     double g;
@@ -204,6 +212,7 @@ typedef struct fblts_params {
     void *stream;
     int32_t use_graph;
     int32_t split;
+    int32_t scheme;
 } fblts_params;
 
 /* Allocates the device state (one arena), uploads h0[nC], u0[nE] and the

@@ -20,6 +20,7 @@ from . import build as _build
 
 OK, E_ARG, E_MESH, E_REGIONS, E_OOM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE = range(9)
 FP64, FP32_TENDENCY = 0, 1
+SCHEME_FBLTS, SCHEME_RK4 = 0, 1
 FORCE_WIND_STRESS, FORCE_BOTTOM_DRAG, FORCE_VORTEX = 1, 2, 4
 PAPER_BETA = (0.531, 0.531, 0.313)   # Sec. 2.1, CFL-optimised FB weights
 
@@ -50,7 +51,7 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("forcing", C.c_int32), ("wind_u", C.c_double),
                 ("wind_v", C.c_double), ("cd", C.c_double), ("rho0", C.c_double),
                 ("rho_air", C.c_double), ("vortex", C.c_double * 9), ("t0", C.c_double),
-                ("stream", C.c_void_p), ("use_graph", C.c_int32), ("split", C.c_int32)]
+                ("stream", C.c_void_p), ("use_graph", C.c_int32), ("split", C.c_int32), ("scheme", C.c_int32)]
 
 
 class FbltsError(RuntimeError):
@@ -280,7 +281,8 @@ def mesh_get_info(mesh):
 
 
 def make_params(dt, g=9.80616, beta=PAPER_BETA, precision=FP64, forcing=0, wind=(0.0, 0.0), cd=0.0,
-                rho0=1025.0, rho_air=1.225, vortex=None, t0=0.0, stream=None, use_graph=True, split=False):
+                rho0=1025.0, rho_air=1.225, vortex=None, t0=0.0, stream=None, use_graph=True, split=False,
+                scheme=0):
     p = Params()
     p.g, p.dt = g, dt
     p.beta[:] = list(beta)
@@ -293,6 +295,7 @@ def make_params(dt, g=9.80616, beta=PAPER_BETA, precision=FP64, forcing=0, wind=
     p.stream = stream
     p.use_graph = int(bool(use_graph))
     p.split = int(bool(split))
+    p.scheme = int(scheme)
     return p
 
 

@@ -350,15 +350,15 @@ static void cached_schedule(const fblts_mesh *m, const fblts_params *p, Schedule
     const bool split = p->split != 0;
     for (const auto &c : m->sched_cache)
         if (c.dt == p->dt && c.beta[0] == p->beta[0] && c.beta[1] == p->beta[1] && c.beta[2] == p->beta[2] &&
-            c.f32 == f32 && c.forcing == p->forcing && c.split == split) {
+            c.f32 == f32 && c.forcing == p->forcing && c.split == split && c.scheme == p->scheme) {
             out = c.sched;
             return;
         }
     Schedule s;
-    build_schedule(m->hm, p->dt, p->beta, trisk, split, s);
+    build_schedule(m->hm, p->dt, p->beta, trisk, split, p->scheme == FBLTS_SCHEME_RK4, s);
     schedule_bytes(m->hm, p->forcing, f32, s);
     if (m->sched_cache.size() < 8)
-        m->sched_cache.push_back({p->dt, {p->beta[0], p->beta[1], p->beta[2]}, f32, p->forcing, split, s});
+        m->sched_cache.push_back({p->dt, {p->beta[0], p->beta[1], p->beta[2]}, f32, p->forcing, split, p->scheme, s});
     out = std::move(s);
 }
 
@@ -391,6 +391,14 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         return FBLTS_E_ARG;
     }
     if (p->forcing & ~7) { set_error("state_init: unknown forcing bits"); return FBLTS_E_ARG; }
+    if (p->scheme != FBLTS_SCHEME_FBLTS && p->scheme != FBLTS_SCHEME_RK4) {
+        set_error("state_init: unknown scheme %d", p->scheme);
+        return FBLTS_E_ARG;
+    }
+    if (p->scheme == FBLTS_SCHEME_RK4 && (m->hm.L != 1 || p->split)) {
+        set_error("state_init: RK4 needs a one-level mesh and split = 0");
+        return FBLTS_E_ARG;
+    }
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev != m->device) { set_error("state_init: current device differs from the mesh's"); return FBLTS_E_ARG; }

@@ -105,7 +105,13 @@ enum SegMode : int {
     SEG_ACC_SET = 3,  // correction sum: acc = tendency
     SEG_ACC_ADD = 4,  // correction sum: acc += tendency
     SEG_KONLY = 5,    // cells: kinetic energy only
-    SEG_PHI = 6       // edges: write the tendency itself (us_out = Phi)
+    SEG_PHI = 6,      // edges: write the tendency itself (us_out = Phi)
+    // classical RK4: the stage array as SEG_UPD and the weighted sum of the
+    // stage tendencies in the correction-sum array (set with weight 1, add
+    // with weight 2), then the step X = X + (tau/6)(sum + tendency) in place
+    SEG_RK_SET = 7,
+    SEG_RK_ADD2 = 8,
+    SEG_RK_FIN = 9
 };
 
 struct Seg {
@@ -123,7 +129,7 @@ struct Op {
     int nseg = 0;
     Seg seg[MAX_SEG];
     int lo = 0, hi = 0;               // launch covers [lo, hi)
-    int stage = 1;                    // 1..3
+    int stage = 1;                    // 1..3 (RK4: 1..4)
     int in_u = A_U, in_h = A_H;       // tendency arguments (u, h) of the stage
     int h0 = A_H, u0 = A_U;           // time level the stage starts from
     int hprev = A_HS2;                // stage-3 FB average uses the stage-2 h
@@ -152,7 +158,9 @@ struct Schedule {
 // (OP_EPREP over the edges and their neighbours)
 // split: the operator splitting of Sec. 3.2 (a slow-term evaluation at the
 // start of every coarse step, stages without the vertex / TRiSK passes)
-void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, bool split,
+// rk4: one step of the classical four-stage RK4 on a one-level mesh instead
+// of an FB-LTS coarse step (beta and split unused)
+void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, bool split, bool rk4,
                     Schedule &s);
 // fills Op::alg_bytes of every op (forcing: the edge passes read the forcing fields)
 void schedule_bytes(const HostMesh &hm, int forcing_flags, bool fp32, Schedule &s);

@@ -27,13 +27,14 @@ struct fblts_mesh {
     void *dbase = nullptr;
     fblts::DevMesh dm{};
     int *cell_n2o = nullptr, *cell_o2n = nullptr, *edge_n2o = nullptr, *edge_o2n = nullptr;
-    // launch lists built for states on this mesh, by (dt, beta, precision, forcing, splitting)
+    // launch lists built for states on this mesh, by (dt, beta, precision, forcing, splitting, scheme)
     struct CachedSchedule {
         double dt;
         double beta[3];
         bool f32;
         int forcing;
         bool split;
+        int scheme;
         fblts::Schedule sched;
     };
     mutable std::mutex cache_mu;

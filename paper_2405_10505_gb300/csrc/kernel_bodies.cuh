@@ -160,6 +160,20 @@ FB_HD void cell_body(const DevMesh &m, const CellArgs &a, int i) {
         } break;
         case SEG_ACC_SET: a.acc[i] = psi; break;
         case SEG_ACC_ADD: a.acc[i] += psi; break;
+        case SEG_RK_SET:
+        case SEG_RK_ADD2: {
+            const double h0 = a.h0[i];
+            const double hn = h0 + a.cdt * psi;
+            a.hs_out[i] = hn;
+            a.hst_out[i] = a.fb_a * hn + a.fb_b * a.hprev[i] + a.fb_c * h0;
+            a.acc[i] = mode == SEG_RK_SET ? psi : a.acc[i] + 2.0 * psi;
+        } break;
+        case SEG_RK_FIN: {
+            const double h0 = a.h_state[i];
+            const double hn = h0 + a.cdt * (a.acc[i] + psi);
+            a.hst_out[i] = a.fb_a * hn + a.fb_b * a.hprev[i] + a.fb_c * h0;
+            a.h_state[i] = hn;
+        } break;
         default: break;
     }
 }
@@ -239,6 +253,12 @@ FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, 
         case SEG_ACC_SET: a.acc[e] = phi; break;
         case SEG_ACC_ADD: a.acc[e] += phi; break;
         case SEG_PHI: a.us_out[e] = m.ebnd[e] ? 0.0 : phi; break;
+        case SEG_RK_SET:
+        case SEG_RK_ADD2:
+            a.us_out[e] = m.ebnd[e] ? 0.0 : a.u0[e] + a.cdt * phi;
+            a.acc[e] = mode == SEG_RK_SET ? phi : a.acc[e] + 2.0 * phi;
+            break;
+        case SEG_RK_FIN: a.u_state[e] = m.ebnd[e] ? 0.0 : a.u_state[e] + a.cdt * (a.acc[e] + phi); break;
         default: break;
     }
 }

@@ -218,7 +218,7 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     FB_UNROLL
     for (int j = 0; j < NMAX; ++j)
         F[j] = (!ROWS || j < ROW_MAIN || n > ROW_MAIN) ? (He[j] + 0.5f * (xi_i + a.xi_in[nb[j]])) * ue[j] : 0.f;
-    if (mode == SEG_UPD) {
+    if (mode == SEG_UPD || mode == SEG_RK_SET || mode == SEG_RK_ADD2) {
         float S = 0.f;
         FB_UNROLL
         for (int j = 0; j < NMAX; ++j) S += sdv[j] * F[j];
@@ -227,7 +227,7 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
         a.xi_out[i] = xn;
         const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;   // the stage-2 value enters stage 3 only
         a.hst_out[i] = a.fb_a * xn + a.fb_b * xp + a.fb_c * x0;
-        return;
+        if (mode == SEG_UPD) return;
     }
     double S = 0.0;
     FB_UNROLL
@@ -245,6 +245,17 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
         } break;
         case SEG_ACC_SET: a.acc[i] = psi; break;
         case SEG_ACC_ADD: a.acc[i] += psi; break;
+        case SEG_RK_SET: a.acc[i] = psi; break;          // RK4: the tendency sum in double
+        case SEG_RK_ADD2: a.acc[i] += 2.0 * psi; break;
+        case SEG_RK_FIN: {
+            const float x0 = a.xi0[i];
+            const double hn = a.h_state[i] + a.cdt * (a.acc[i] + psi);
+            const float xn = (float)(hn + a.bottom[i]);
+            a.h_state[i] = hn;
+            a.xi_shadow[i] = xn;
+            const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;
+            a.hst_out[i] = a.fb_a * xn + a.fb_b * xp + a.fb_c * x0;
+        } break;
         default: break;
     }
 }
@@ -394,6 +405,16 @@ FB_HD void edge32_apply(const A &a, int mode, int e, bool bnd, float phi) {
         case SEG_ACC_SET: a.acc[e] = (double)phi; break;
         case SEG_ACC_ADD: a.acc[e] += (double)phi; break;
         case SEG_PHI: a.us_out[e] = bnd ? 0.f : phi; break;
+        case SEG_RK_SET:
+        case SEG_RK_ADD2:
+            a.us_out[e] = bnd ? 0.f : a.u0[e] + (float)a.cdt * phi;
+            a.acc[e] = mode == SEG_RK_SET ? (double)phi : a.acc[e] + 2.0 * (double)phi;
+            break;
+        case SEG_RK_FIN: {
+            const double un = bnd ? 0.0 : a.u_state[e] + a.cdt * (a.acc[e] + (double)phi);
+            a.u_state[e] = un;
+            a.u_shadow[e] = (float)un;
+        } break;
         default: break;
     }
 }
@@ -511,7 +532,11 @@ FB_HD void final32_body(const IfArgs32 &a, const unsigned char *ebnd, int t) {
 // Moving Holland-type vortex in float (the FP32 path): the offset from the
 // centre is formed in double, the profile p = pc + dp exp(-(R/r)^B) and the
 // gradient wind V = sqrt(B dp/rho_air (R/r)^B exp(-(R/r)^B) + (r f/2)^2) - r f/2
-// in float; returns p - (pc + dp), the pressure relative to ambient.
+// in float; returns p - (pc + dp), the pressure relative to ambient.  Both are
+// taken in forms without cancellation where (R/r)^B is small (far from the
+// centre, where neighbouring cells differ by a tiny fraction of the pressure
+// anomaly): p - (pc + dp) = dp expm1(-(R/r)^B), and with X the first term
+// under the root, V = X / (sqrt(X + (r f/2)^2) + r f/2).
 FB_HD float vortex_at32(const DevForcing &fz, double x, double y, double t, float &wu, float &wv) {
     const float rx = (float)(x - (fz.vx[4] + fz.vx[6] * t)), ry = (float)(y - (fz.vx[5] + fz.vx[7] * t));
     const float r = sqrtf(rx * rx + ry * ry);
@@ -522,10 +547,12 @@ FB_HD float vortex_at32(const DevForcing &fz, double x, double y, double t, floa
     const float ex = expf(-A);
     if (ex == 0.f) return -(float)fz.vx[1];
     const float hf = 0.5f * r * (float)fz.vx[8];
-    const float V = sqrtf((float)fz.vx[3] * (float)fz.vx[1] / (float)fz.rho_air * A * ex + hf * hf) - hf;
+    const float X = (float)fz.vx[3] * (float)fz.vx[1] / (float)fz.rho_air * A * ex;
+    const float den = sqrtf(X + hf * hf) + hf;
+    const float V = den > 0.f ? X / den : 0.f;
     wu = -V * ry / r;
     wv = V * rx / r;
-    return (float)fz.vx[1] * (ex - 1.f);
+    return (float)fz.vx[1] * expm1f(-A);
 }
 
 // Float copies of the forcing fields: ps32 relative to the ambient pc + dp.

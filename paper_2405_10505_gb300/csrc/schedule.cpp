@@ -38,18 +38,22 @@ struct AccInfo {
 
 class Builder {
 public:
-    Builder(const HostMesh &hm, const double beta[3], bool trisk_cells, bool split, Schedule &s)
-        : hm_(hm), s_(s), trisk_cells_(trisk_cells), split_(split) {
+    Builder(const HostMesh &hm, const double beta[3], bool trisk_cells, bool split, bool rk4, Schedule &s)
+        : hm_(hm), s_(s), trisk_cells_(trisk_cells), split_(split), rk4_(rk4) {
         b_[0] = beta[0]; b_[1] = beta[1]; b_[2] = beta[2];
     }
 
-    void top(double dt) { step(0, dt, AccInfo{}); }
+    void top(double dt) {
+        if (rk4_) rk4(dt);
+        else step(0, dt, AccInfo{});
+    }
 
 private:
     const HostMesh &hm_;
     Schedule &s_;
     bool trisk_cells_;
     bool split_;
+    bool rk4_;
     double b_[3];
     std::map<std::pair<int, int>, std::array<int, 6>> memo_;
 
@@ -122,12 +126,14 @@ private:
 
     // one FB-RK stage: cell segments, edge segments, arrays, coefficient
     void stage(int s, double tau, std::vector<Seg> csegs, std::vector<Seg> esegs) {
-        const int in_u = s == 1 ? A_U : (s == 2 ? A_US1 : A_US2);
-        const int in_h = s == 1 ? A_H : (s == 2 ? A_HS1 : A_HS2);
-        const int hst = s == 1 ? A_HST1 : (s == 2 ? A_HST2 : A_HST3);
-        const int out_h = s == 1 ? A_HS1 : (s == 2 ? A_HS2 : A_HS3);
-        const int out_u = s == 1 ? A_US1 : (s == 2 ? A_US2 : A_US3);
-        const double cdt = (s == 1 ? tau / 3.0 : (s == 2 ? tau / 2.0 : tau));
+        static const int U_OF[4] = {A_U, A_US1, A_US2, A_US3}, H_OF[4] = {A_H, A_HS1, A_HS2, A_HS3};
+        static const int HST_OF[4] = {A_HST1, A_HST2, A_HST3, A_HST1};
+        const int in_u = U_OF[s - 1], in_h = H_OF[s - 1];
+        const int hst = HST_OF[s - 1];
+        const int out_h = H_OF[s < 4 ? s : 0], out_u = U_OF[s < 4 ? s : 0];
+        // FB-RK(3,2): c = 1/3, 1/2, 1; RK4: c = 1/2, 1/2, 1 and the final tau/6
+        const double cdt = rk4_ ? (s == 1 || s == 2 ? tau / 2.0 : (s == 3 ? tau : tau / 6.0))
+                                : (s == 1 ? tau / 3.0 : (s == 2 ? tau / 2.0 : tau));
         // dependency ranges of the edge pass
         int elo = INT32_MAX, ehi = -1;
         for (auto &g : esegs) if (g.end > g.begin) { elo = std::min(elo, g.begin); ehi = std::max(ehi, g.end); }
@@ -146,6 +152,11 @@ private:
         if (s == 1) { c.fb_a = b_[0]; c.fb_b = 0.0; c.fb_c = 1.0 - b_[0]; }
         if (s == 2) { c.fb_a = b_[1]; c.fb_b = 0.0; c.fb_c = 1.0 - b_[1]; }
         if (s == 3) { c.fb_a = b_[2]; c.fb_b = 1.0 - 2.0 * b_[2]; c.fb_c = b_[2]; }
+        if (rk4_) {
+            // RK4 evaluates Phi at the stage's input state: the "average" is that state
+            c.hprev = in_h;
+            c.fb_a = 0.0; c.fb_b = 1.0; c.fb_c = 0.0;
+        }
         int clo = INT32_MAX, chi = -1;
         for (auto &g : csegs) {
             if (g.end <= g.begin) continue;
@@ -247,6 +258,17 @@ private:
     void step(int l, double tau, const AccInfo &acc) {
         if (l + 1 >= hm_.L) fbrk(l, tau, acc);
         else fblts(l, tau, acc);
+    }
+
+    // Classical RK4 on every cell and edge (the comparison integrator of
+    // Sec. 4.2): stage s evaluates the tendencies T_s at the state of stage
+    // s-1, writes X_s = X^n + c_s tau T_s (c = 1/2, 1/2, 1) and sums
+    // T_1 + 2 T_2 + 2 T_3 in the correction-sum arrays; stage 4 applies
+    // X^{n+1} = X^n + (tau/6)(sum + T_4) in place.
+    void rk4(double tau) {
+        static const int MODE[4] = {SEG_RK_SET, SEG_RK_ADD2, SEG_RK_ADD2, SEG_RK_FIN};
+        for (int s = 1; s <= 4; ++s)
+            stage(s, tau, {Seg{0, hm_.nC, MODE[s - 1]}}, {Seg{0, hm_.nE, MODE[s - 1]}});
     }
 };
 
@@ -360,6 +382,14 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
             if (mode == SEG_ACC_SET) x = n * 8;
             if (mode == SEG_ACC_ADD) x = n * 16;
             if (mode == SEG_PHI) x = n * R;
+            // RK4: as SEG_UPD (the previous stage is the element's own input) plus
+            // the tendency sum (write, or read and write); the final stage as
+            // SEG_INPLACE plus the sum read
+            if (mode == SEG_RK_SET || mode == SEG_RK_ADD2) x = n * ((cell ? 3 : 2) * R + (mode == SEG_RK_SET ? 8 : 16));
+            if (mode == SEG_RK_FIN) {
+                if (cell) x = fp32 ? n * (16 + 8 + 4 + 4 + 4 + 8) : n * (16 + 8 + 8);
+                else x = fp32 ? n * (16 + 4 + 8) : n * (16 + 8);
+            }
             return x;
         };
         switch (op.kind) {
@@ -459,13 +489,13 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
     }
 }
 
-void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, bool split,
+void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, bool split, bool rk4,
                     Schedule &s) {
     s.ops.clear();
     Op fz;
     fz.kind = OP_FORCING;
     s.ops.push_back(fz);
-    if (split) {
+    if (split && !rk4) {
         // the slow part of Phi (Coriolis, kinetic-energy gradient, forcing) at
         // the coarse step's start time level (h^n, u^n), on every edge
         // [Sec. 3.2, Eq. splitting]
@@ -487,7 +517,7 @@ void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool tr
         e.seg[0] = Seg{0, hm.nE, SEG_PHI}; e.nseg = 1; e.lo = 0; e.hi = hm.nE;
         s.ops.push_back(e);
     }
-    Builder b(hm, beta, trisk_cells, split, s);
+    Builder b(hm, beta, trisk_cells, split && !rk4, rk4, s);
     b.top(dt);
     Op se;
     se.kind = OP_STEP_END;

@@ -16,15 +16,16 @@ def forcing_flags(s):
     return flags
 
 
-def make_state(s, M=None, level=None, use_graph=True, precision=fb.FP64, mesh=None, split=False):
+def make_state(s, M=None, level=None, use_graph=True, precision=fb.FP64, mesh=None, split=False,
+               scheme=fb.SCHEME_FBLTS, dt=None):
     lev = s.level if level is None else level
     Ms = s.M if M is None else M
     mesh = mesh or fb.mesh_create(s.mesh, s.fVertex, level=lev, M=Ms)
     fz = s.forcing
     vt = list(fz.vortex) + [float(np.mean(s.fVertex))] if fz.vortex is not None else None
-    p = fb.make_params(s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
+    p = fb.make_params(s.dt if dt is None else dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
                        rho0=fz.rho0, rho_air=fz.rho_air, vortex=vt, use_graph=use_graph, precision=precision,
-                       split=split)
+                       split=split, scheme=scheme)
     return fb.state_init(mesh, p, s.h0, s.u0, s.bottom)
 
 
