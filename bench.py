@@ -33,32 +33,29 @@ METRIC = "SWE cell-updates/s (% HBM peak), FP32 vs FP64 at stated err; p50/p99 l
 UNIT = "cell-updates/s"
 
 
-def make_workload(name):
-    from synth import scenario
-    if name == "shelf":
-        s = scenario.shelf_case()
-        desc = ("periodic-in-y 512x512 hex channel, dc 2 km, walls in x, tanh shelf 10-4000 m with 5% "
-                "roughness, 2 LTS levels (M=4) by gravity-wave CFL, 15 m/s wind stress + quadratic drag")
-    elif name == "basin":
-        from synth import basin
-        s = basin.basin_case()
-        desc = ("closed basin, variable-resolution Voronoi mesh (~2.0M cells): 500 m along a seeded sinuous "
-                "coast growing to 20 km offshore, depth 5-4000 m, 3 LTS levels (M=8) by gravity-wave CFL, "
-                "moving Holland vortex with wind stress, pressure gradient and quadratic drag")
-    elif name == "basin_small":
-        from synth import basin
-        s = basin.basin_case(Ly=1200e3)
-        desc = "1/8-length sample of the basin workload (same recipe, Ly 1200 km, ~0.25M cells)"
-    elif name == "basin_tiny":
-        from synth import basin
-        s = basin.basin_case(Ly=150e3)
-        desc = "1/64-length sample of the basin workload (same recipe, Ly 150 km, ~32k cells)"
-    elif name == "bump":
-        s = scenario.gaussian_bump_case(two_level=True)
-        desc = "doubly periodic 32x32 hex, flat 1000 m, Gaussian bump, 2 LTS levels (M=2)"
-    else:
+def make_workload(name, build=True):
+    """The named synthetic workload and its description (build=False: the
+    description only)."""
+    from synth import basin, scenario
+    table = {
+        "shelf": (scenario.shelf_case,
+                  "periodic-in-y 512x512 hex channel, dc 2 km, walls in x, tanh shelf 10-4000 m with 5% "
+                  "roughness, 2 LTS levels (M=4) by gravity-wave CFL, 15 m/s wind stress + quadratic drag"),
+        "basin": (basin.basin_case,
+                  "closed basin, variable-resolution Voronoi mesh (~2.0M cells): 500 m along a seeded sinuous "
+                  "coast growing to 20 km offshore, depth 5-4000 m, 3 LTS levels (M=8) by gravity-wave CFL, "
+                  "moving Holland vortex with wind stress, pressure gradient and quadratic drag"),
+        "basin_small": (lambda: basin.basin_case(Ly=1200e3),
+                        "1/8-length sample of the basin workload (same recipe, Ly 1200 km, ~0.25M cells)"),
+        "basin_tiny": (lambda: basin.basin_case(Ly=150e3),
+                       "1/64-length sample of the basin workload (same recipe, Ly 150 km, ~32k cells)"),
+        "bump": (lambda: scenario.gaussian_bump_case(two_level=True),
+                 "doubly periodic 32x32 hex, flat 1000 m, Gaussian bump, 2 LTS levels (M=2)"),
+    }
+    if name not in table:
         raise SystemExit(f"unknown workload {name}")
-    return s, desc
+    make, desc = table[name]
+    return (make() if build else None), desc
 
 
 def peaks():
@@ -149,20 +146,45 @@ def traffic_for(workload, precision, kernel):
     return ent.get("dram_bytes_per_launch")
 
 
-def oracle_sample(s, budget_s=15.0):
-    """Times the FP64 oracle on whole coarse steps of the workload (single thread)."""
+def oracle_sample(s, budget_s=15.0, threads=1):
+    """Times the FP64 oracle on whole coarse steps of the workload.
+
+    The oracle is single-threaded; with threads > 1 one instance per thread
+    advances its own copy of the state (the C library runs without the
+    interpreter lock), so the host's cores all work, as replicas.  Returns
+    the steps of all instances, the wall time, and the state and step count
+    of the first instance."""
+    import threading
+
     import oracle
     m = oracle.Mesh.from_scenario(s)
     p = oracle.scenario_params(s)
-    h, u = s.h0.copy(), s.u0.copy()
-    n, t0 = 0, time.perf_counter()
-    while True:
-        h, u = oracle.fblts(m, p, s.level, s.M, h, u, s.dt, 1, t0=n * s.dt)
-        n += 1
-        if time.perf_counter() - t0 >= budget_s or n >= 50:
-            break
+    oracle.lib()
+    out = [None] * threads
+    t0 = time.perf_counter()
+
+    def run(i):
+        h, u = s.h0.copy(), s.u0.copy()
+        n = 0
+        while True:
+            h, u = oracle.fblts(m, p, s.level, s.M, h, u, s.dt, 1, t0=n * s.dt)
+            n += 1
+            if time.perf_counter() - t0 >= budget_s or n >= 50:
+                break
+        out[i] = (n, h, u)
+
+    workers = [threading.Thread(target=run, args=(i,)) for i in range(threads)]
+    for w in workers:
+        w.start()
+    for w in workers:
+        w.join()
     el = time.perf_counter() - t0
-    return n, el, h, u
+    return sum(o[0] for o in out), el, out[0][1], out[0][2], out[0][0]
+
+
+def cpu_threads(args):
+    """Oracle instances for the CPU legs: --cpu-threads, else one per host core."""
+    return args.cpu_threads if args.cpu_threads > 0 else (os.cpu_count() or 1)
 
 
 def forcing_flags(s):
@@ -211,35 +233,40 @@ def fbrk32_imag_limit(beta):
     return lo
 
 
-def reference_sample(workload, s):
+def reference_sample(workload):
     """The workload the oracle times per step: the workload itself, or for the
     2M-cell basin (about 100 s per oracle coarse step) its 1/64-length sample
     (about 1.5 s per step, so a run of ~100 steps ends within a few minutes)."""
     if workload == "basin":
         ws, _ = make_workload("basin_tiny")
         return ws, "basin_tiny (1/64-length sample of the basin: same recipe, Ly 150 km, 31.7k cells)"
-    return s, workload
+    ws, _ = make_workload(workload)
+    return ws, workload
 
 
-def run_reference(args, s, desc, rank):
+def run_reference(args, rank):
+    """The reference arm: the oracle on the host cores (rank 0 only)."""
     if rank != 0:
         return
-    ws, sample_name = reference_sample(args.workload, s)
+    _, desc = make_workload(args.workload, build=False)
+    ws, sample_name = reference_sample(args.workload)
+    T = cpu_threads(args)
     for _ in range(args.warmup):
-        oracle_sample(ws, budget_s=0.0)
+        oracle_sample(ws, budget_s=0.0, threads=T)
     cu = cell_updates_per_step(ws)
     times = []
     for k in range(args.steps):
-        n, el, _, _ = oracle_sample(ws, budget_s=0.0)
+        n, el, _, _, _ = oracle_sample(ws, budget_s=0.0, threads=T)
         times.append(el / n)
     ms = 1000.0 * statistics.mean(times)
     v = cu / (ms / 1000.0)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": desc, "cells": int(s.mesh.nCells)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} whole coarse steps of {sample_name}, single-thread C oracle"},
+            "config": {"workload": args.workload, "description": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": T, "kind": "oracle",
+                             "sample": f"{args.steps} steps, each one whole coarse step of {sample_name} on each "
+                                       f"of {T} threads (one single-threaded C oracle instance per host core)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -467,6 +494,8 @@ def main():
     ap.add_argument("--workload", default="basin")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="oracle instances for the CPU legs (default: one per host core)")
     ap.add_argument("--members", type=int, default=48, help="ensemble workload: members")
     ap.add_argument("--member-cells", default="20000,800000",
                     help="ensemble workload: range of member sizes (cells), lo,hi")
@@ -491,10 +520,10 @@ def main():
     if args.workload == "serve" and args.impl != "reference":
         run_serve(args, rank)
         return
-    s, desc = make_workload(args.workload)
     if args.impl == "reference":
-        run_reference(args, s, desc, rank)
+        run_reference(args, rank)
         return
+    s, desc = make_workload(args.workload)
 
     import torch
     import paper_2405_10505_gb300 as fb
@@ -613,6 +642,17 @@ def main():
         line["split"] = {"value": cu / (sms / 1000.0), "ms_per_step": sms, "speedup_vs_unsplit": ms_step / sms,
                          "alg_bytes_per_step": sb, "step_hbm_frac": sb / (sms / 1000.0) / 1e9 / hbm}
         fb.state_destroy(sst)
+        # its variant with the slow terms of every finer level evaluated once per
+        # step of that level (proposed at the end of Sec. 4.2)
+        if int(info.nLevels) > 1:
+            sst = fb.state_init(mesh, fb.make_params(
+                s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd, rho0=fz.rho0,
+                rho_air=fz.rho_air, vortex=vt, precision=prec, stream=stream.cuda_stream, use_graph=True, split=2),
+                s.h0, s.u0, s.bottom)
+            fms = timed_steps(fb, torch, sst, stream, 3, max(3, min(args.steps, 20)))
+            line["split_per_level_step"] = {"value": cu / (fms / 1000.0), "ms_per_step": fms,
+                                            "speedup_vs_unsplit": ms_step / fms}
+            fb.state_destroy(sst)
         # global FB-RK(3,2) at the finest level's step on the same mesh (no LTS):
         # the time one coarse step's simulated interval takes without local time stepping
         nl = int(info.nLevels)
@@ -659,10 +699,13 @@ def main():
         if args.workload == "basin":
             ws, _ = make_workload("basin_small")
             sample_name = "basin_small (1/8-length sample of the basin: same recipe, Ly 1200 km)"
-        n, el, ho, uo = oracle_sample(ws)
-        line["cpu_baseline"] = {"value": cell_updates_per_step(ws) * n / el, "unit": UNIT, "cores": 1,
+        T = cpu_threads(args)
+        nt, el, ho, uo, n = oracle_sample(ws, threads=T)
+        line["cpu_baseline"] = {"value": cell_updates_per_step(ws) * nt / el, "unit": UNIT, "cores": T,
                                 "kind": "oracle",
-                                "sample": f"{n} whole coarse steps of {sample_name}, single-thread C oracle",
+                                "sample": f"{nt} whole coarse steps of {sample_name} in {el:.1f} s over {T} threads "
+                                          "(one single-threaded C oracle instance per host core, each on its own "
+                                          "copy of the state)",
                                 "host_cores_available": os.cpu_count()}
         # error of this path against the oracle on the same window
         wmesh = mesh if ws is s else fb.mesh_create(ws.mesh, ws.fVertex, level=ws.level, M=ws.M)

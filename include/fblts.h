@@ -184,12 +184,19 @@ enum {
  *  t0            time of the initial state (s).
  *  stream        cudaStream_t to issue work on, or NULL for an own stream.
  *  use_graph     non-zero: capture one coarse step as a CUDA graph.
- *  split         non-zero: the fast/slow operator splitting of Sec. 3.2
+ *  split         1: the fast/slow operator splitting of Sec. 3.2
  *                (Eq. splitting): inside a coarse step Phi is replaced by the
  *                pressure gradient -g grad(h + b) at the stage state plus the
  *                remaining terms (Coriolis, kinetic-energy gradient, forcing)
  *                evaluated once at the coarse step's start time level; Psi is
- *                not split.  First order in time.
+ *                not split.  First order in time.  split = 2: as 1, and the
+ *                slow terms of the edges of every finer level are evaluated
+ *                again at the start of each of that level's steps (fine
+ *                cells at their current state, IF-1 at the predictions of
+ *                Eq. preds), so the fine region advances its slow part with
+ *                its own step; coarse edges, the interface correction
+ *                included, keep the values of the coarse step's start.  This
+ *                is the variant proposed at the end of Sec. 4.2.
  *  scheme        FBLTS_SCHEME_FBLTS (0): FB-LTS (Sec. 2.2; on a one-level mesh
  *                global FB-RK(3,2), Eq. fbrk32).  FBLTS_SCHEME_RK4 (1): the
  *                classical four-stage Runge-Kutta scheme, the paper's

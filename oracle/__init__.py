@@ -17,6 +17,10 @@ Parity status of each function (what pins it; see the tests under
   (Theorem 1), shrinking-set vs full-band agreement (bitwise), prediction
   exactness on linear data, second-order convergence against ``rk4``.
 * ``rk4`` - fourth-order convergence on the linear mode.
+* ``fblts(..., split)`` (Sec. 3.2 splitting; 2: its per-fine-step variant of
+  Sec. 4.2) - fast + slow parts add up to Phi, bitwise reductions (no slow
+  terms, M = 1, one level), mass conservation, first order against ``rk4``,
+  forward-Euler closed forms of the slow Coriolis term on an f-plane.
 * forcing terms (wind stress, bottom drag, pressure gradient) - parity
   unpinned beyond closed forms on uniform fields (the paper gives no
   coefficients).
@@ -130,9 +134,11 @@ class Mesh:
 
 def params(g=GRAV, beta=BETA, terms=T_FULL, H_lin=0.0, forcing=None, f0=None, split=False):
     """Oracle parameters; ``forcing`` is a ``synth.scenario.Forcing`` or None;
-    ``split`` selects the fast/slow operator splitting of Sec. 3.2."""
+    ``split`` selects the fast/slow operator splitting of Sec. 3.2 (1 or True), or
+    its variant with the slow terms of the finer levels re-evaluated once per
+    fine step (2, proposed in Sec. 4.2)."""
     p = Params(g, beta[0], beta[1], beta[2], terms, H_lin, 0.0, 0.0, 0, 0.0, 1025.0, 1.225,
-               0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, int(bool(split)))
+               0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, int(split))
     if forcing is not None and forcing.any:
         p.terms |= T_FORCING
         p.wind_u, p.wind_v = forcing.wind_u, forcing.wind_v

@@ -78,7 +78,8 @@ typedef struct {
     double cd, rho0, rho_air;
     int vortex;
     double vx_pc, vx_dp, vx_rmax, vx_B, vx_x0, vx_y0, vx_vx, vx_vy, vx_f0;
-    int split;   /* 1: fast/slow operator splitting of Phi (Sec. 3.2) */
+    int split;   /* 1: fast/slow operator splitting of Phi (Sec. 3.2); 2: its slow terms
+                    re-evaluated at the start of every fine step (Sec. 4.2) */
 } om_params;
 
 static const double OM_NAN = (double)NAN;
@@ -248,7 +249,13 @@ static double om_phi_edge(const om_mesh *m, const om_params *p, const om_forcing
  * Phi_fast = -g grad(h + b) (the external gravity-wave term) and Phi_slow the
  * remaining terms (Coriolis, kinetic-energy gradient, forcing), evaluated once
  * per coarse step from its start time level; Psi is not split.  `slow` holds
- * Phi_slow per edge (NULL: no splitting). */
+ * Phi_slow per edge (NULL: no splitting).
+ * p->split == 2 is the variant the paper proposes at the end of Sec. 4.2:
+ * while the fine region advances, the slow terms of its edges are evaluated
+ * once per fine step, at t^{n,k} (fine cells at their current state, IF-1 at
+ * the predictions X^{n,k} of Eq. preds), so the slow subsystem advances with
+ * the fine step there; coarse edges, the interface correction included, keep
+ * the values of t^n.  With more levels this holds per level pair. */
 static double om_phi_stage(const om_mesh *m, const om_params *p, const om_forcing *fz, const double *slow,
                            const double *u, const double *h, const double *K, const double *q, int e) {
     if (!slow) return om_phi_edge(m, p, fz, u, h, K, q, e);
@@ -803,7 +810,23 @@ static int om_fblts_region(om_ctx *c, int l, double tau, double *h, double *u, c
     for (int k = 0; k < Mk && c->status == OM_OK; ++k) {
         om_bnd in = {cIF1, eIF1, hP[k], uP[k], hP13[k], uP13[k], sP1[k], hP12[k], uP12[k], sP2[k], sP3[k]};
         fH2[k] = nan_cells(c); fU2[k] = nan_edges(c); fS3[k] = nan_cells(c);
+        const double *outer = c->slow;
+        double *slow_k = NULL;
+        if (p->split == 2) {
+            /* slow terms of the fine edges at t^{n,k}: fine cells and edges as they
+             * stand after k subcycles, IF-1 at the predictions, the rest undefined */
+            double *Hk = nan_cells(c), *Uk = nan_edges(c);
+            put_cells(c, Hk, h, cFine); put_edges(c, Uk, u, eFine);
+            put_cells(c, Hk, hP[k], cIF1); put_edges(c, Uk, uP[k], eIF1);
+            double *fresh = om_slow_terms(m, p, c->fz, Uk, Hk);
+            slow_k = dalloc(nE);
+            for (int e = 0; e < nE; ++e) slow_k[e] = eFine[e] ? fresh[e] : outer[e];
+            c->slow = slow_k;
+            free(fresh); free(Hk); free(Uk);
+        }
         om_advance(c, l + 1, tau / Md, h, u, &in, fH2[k], fU2[k], fS3[k]);
+        c->slow = outer;
+        free(slow_k);
     }
 
     /* ---- step 4: interface correction on IF-1 and IF-2 [Eq. if_correction] */

@@ -294,7 +294,7 @@ def make_params(dt, g=9.80616, beta=PAPER_BETA, precision=FP64, forcing=0, wind=
     p.t0 = t0
     p.stream = stream
     p.use_graph = int(bool(use_graph))
-    p.split = int(bool(split))
+    p.split = int(split)   # False/True -> 0/1; 2: slow terms per step of every finer level
     p.scheme = int(scheme)
     return p
 

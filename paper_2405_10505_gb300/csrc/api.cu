@@ -347,7 +347,7 @@ static void cached_schedule(const fblts_mesh *m, const fblts_params *p, Schedule
     const bool f32 = p->precision == FBLTS_FP32_TENDENCY;
     const bool trisk = f32 && m->dm.rowS != 0;
     std::lock_guard<std::mutex> lock(m->cache_mu);
-    const bool split = p->split != 0;
+    const int split = p->split;
     for (const auto &c : m->sched_cache)
         if (c.dt == p->dt && c.beta[0] == p->beta[0] && c.beta[1] == p->beta[1] && c.beta[2] == p->beta[2] &&
             c.f32 == f32 && c.forcing == p->forcing && c.split == split && c.scheme == p->scheme) {
@@ -391,6 +391,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         return FBLTS_E_ARG;
     }
     if (p->forcing & ~7) { set_error("state_init: unknown forcing bits"); return FBLTS_E_ARG; }
+    if (p->split < 0 || p->split > 2) { set_error("state_init: split must be 0, 1 or 2"); return FBLTS_E_ARG; }
     if (p->scheme != FBLTS_SCHEME_FBLTS && p->scheme != FBLTS_SCHEME_RK4) {
         set_error("state_init: unknown scheme %d", p->scheme);
         return FBLTS_E_ARG;

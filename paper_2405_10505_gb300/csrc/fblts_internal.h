@@ -157,10 +157,12 @@ struct Schedule {
 // over the cells of the edge pass) instead of per edge from edge records
 // (OP_EPREP over the edges and their neighbours)
 // split: the operator splitting of Sec. 3.2 (a slow-term evaluation at the
-// start of every coarse step, stages without the vertex / TRiSK passes)
+// start of every coarse step, stages without the vertex / TRiSK passes);
+// split = 2 also re-evaluates the slow terms of each finer level's edges at
+// the start of each of its steps (the variant proposed in Sec. 4.2)
 // rk4: one step of the classical four-stage RK4 on a one-level mesh instead
 // of an FB-LTS coarse step (beta and split unused)
-void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, bool split, bool rk4,
+void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, int split, bool rk4,
                     Schedule &s);
 // fills Op::alg_bytes of every op (forcing: the edge passes read the forcing fields)
 void schedule_bytes(const HostMesh &hm, int forcing_flags, bool fp32, Schedule &s);

@@ -33,7 +33,7 @@ struct fblts_mesh {
         double beta[3];
         bool f32;
         int forcing;
-        bool split;
+        int split;
         int scheme;
         fblts::Schedule sched;
     };

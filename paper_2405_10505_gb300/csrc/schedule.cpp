@@ -38,7 +38,7 @@ struct AccInfo {
 
 class Builder {
 public:
-    Builder(const HostMesh &hm, const double beta[3], bool trisk_cells, bool split, bool rk4, Schedule &s)
+    Builder(const HostMesh &hm, const double beta[3], bool trisk_cells, int split, bool rk4, Schedule &s)
         : hm_(hm), s_(s), trisk_cells_(trisk_cells), split_(split), rk4_(rk4) {
         b_[0] = beta[0]; b_[1] = beta[1]; b_[2] = beta[2];
     }
@@ -52,7 +52,7 @@ private:
     const HostMesh &hm_;
     Schedule &s_;
     bool trisk_cells_;
-    bool split_;
+    int split_;   // 0: none, 1: slow terms per coarse step, 2: per step of each level
     bool rk4_;
     double b_[3];
     std::map<std::pair<int, int>, std::array<int, 6>> memo_;
@@ -245,6 +245,7 @@ private:
             pr.fb_a = b_[0]; pr.fb_b = b_[1]; pr.fb_c = b_[2];
             pr.hi = std::max(cIF2 - cb0, eIF2 - eb0);
             s_.ops.push_back(pr);
+            if (split_ == 2) slow_block(eb0);   // the fine region's slow terms at t^{n,k}
             AccInfo in;
             in.on = true; in.c_lo = cb0; in.c_hi = cINT; in.e_lo = eb0; in.e_hi = eINT; in.set = (k == 0);
             step(f, tau / (double)M, in);
@@ -258,6 +259,35 @@ private:
     void step(int l, double tau, const AccInfo &acc) {
         if (l + 1 >= hm_.L) fbrk(l, tau, acc);
         else fblts(l, tau, acc);
+    }
+
+    // The slow part of Phi (Coriolis, kinetic-energy gradient, forcing) on
+    // the edges [0, ehi) from the time level (h, u) as it stands: the K-only
+    // cell pass, the vertex pass and the TRiSK (edge-prep) pass over what
+    // those edges read, then an edge pass writing the slow part per edge
+    // [Sec. 3.2, Eq. splitting].  Before a fine step the time level of the
+    // fine cells is current and IF-1 holds the predictions X^{n,k}.
+    void slow_block(int ehi) {
+        if (ehi <= 0) return;
+        const auto r = deps(0, ehi);
+        Op k;
+        k.kind = OP_CELL; k.stage = 1; k.in_u = A_U; k.in_h = A_H; k.hst = A_H; k.split = 1;
+        k.seg[0] = Seg{r[0], r[1], SEG_KONLY}; k.nseg = 1; k.lo = r[0]; k.hi = r[1];
+        s_.ops.push_back(k);
+        Op v;
+        v.kind = OP_VERT; v.in_u = A_U; v.hst = A_H; v.split = 1;
+        v.seg[0] = Seg{r[4], r[5], SEG_UPD}; v.nseg = 1; v.lo = r[4]; v.hi = r[5];
+        s_.ops.push_back(v);
+        Op p;
+        p.kind = trisk_cells_ ? OP_TRISK : OP_EPREP; p.in_u = A_U; p.hst = A_H; p.split = 1;
+        p.lo = trisk_cells_ ? r[0] : r[2];
+        p.hi = trisk_cells_ ? r[1] : r[3];
+        p.seg[0] = Seg{p.lo, p.hi, SEG_UPD}; p.nseg = 1;
+        s_.ops.push_back(p);
+        Op e;
+        e.kind = OP_EDGE; e.in_u = A_U; e.hst = A_H; e.out_u = A_SLOW; e.split = 1;
+        e.seg[0] = Seg{0, ehi, SEG_PHI}; e.nseg = 1; e.lo = 0; e.hi = ehi;
+        s_.ops.push_back(e);
     }
 
     // Classical RK4 on every cell and edge (the comparison integrator of
@@ -489,7 +519,7 @@ void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
     }
 }
 
-void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, bool split, bool rk4,
+void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, int split, bool rk4,
                     Schedule &s) {
     s.ops.clear();
     Op fz;
@@ -517,7 +547,7 @@ void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool tr
         e.seg[0] = Seg{0, hm.nE, SEG_PHI}; e.nseg = 1; e.lo = 0; e.hi = hm.nE;
         s.ops.push_back(e);
     }
-    Builder b(hm, beta, trisk_cells, split && !rk4, rk4, s);
+    Builder b(hm, beta, trisk_cells, rk4 ? 0 : split, rk4, s);
     b.top(dt);
     Op se;
     se.kind = OP_STEP_END;

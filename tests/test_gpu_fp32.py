@@ -83,15 +83,17 @@ def test_fp32_explicit_neighbour_lists():
     assert dh <= 1e-6 and du <= 1e-5, (dh, du)
 
 
+@pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("name", ["bump_lts_m2", "shelf_vortex_m4", "nested_3level", "jittered_voronoi_m2"])
-def test_fp32_split_parity_with_oracle(name):
-    """Fast/slow operator splitting (Sec. 3.2), FP32 tendencies, against the split oracle."""
+def test_fp32_split_parity_with_oracle(name, split):
+    """Fast/slow operator splitting (Sec. 3.2; split = 2: slow terms per fine
+    step, Sec. 4.2), FP32 tendencies, against the split oracle."""
     make, nsteps, M = CASES[name]
     s = make()
-    st = make_state(s, M=M, precision=fb.FP32_TENDENCY, split=True)
+    st = make_state(s, M=M, precision=fb.FP32_TENDENCY, split=split)
     fb.lts_advance(st, nsteps)
     h, u = fb.state_read(st)
-    ho, uo = oracle.fblts(oracle.Mesh.from_scenario(s), oracle.scenario_params(s, split=True), s.level,
+    ho, uo = oracle.fblts(oracle.Mesh.from_scenario(s), oracle.scenario_params(s, split=split), s.level,
                           s.M if M is None else M, s.h0, s.u0, s.dt, nsteps)
     dh, du = rel_errors(h, u, ho, uo)
     assert dh <= 1e-6 and du <= 1e-5, (dh, du)

@@ -169,16 +169,18 @@ def test_odd_sized_arrays(precision):
 SPLIT_CASES = ["bump_lts_m2", "shelf_forced_m4", "shelf_vortex_m4", "nested_3level", "jittered_voronoi_m2"]
 
 
+@pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("name", SPLIT_CASES)
-def test_split_parity_with_oracle(name):
-    """Fast/slow operator splitting (Sec. 3.2) against the split oracle (FP64, 1e-10)."""
+def test_split_parity_with_oracle(name, split):
+    """Fast/slow operator splitting (Sec. 3.2; split = 2: slow terms per fine
+    step, Sec. 4.2) against the split oracle (FP64, 1e-10)."""
     make, nsteps, M = CASES[name]
     s = make()
-    st = make_state(s, M=M, split=True)
+    st = make_state(s, M=M, split=split)
     fb.lts_advance(st, nsteps)
     h, u = fb.state_read(st)
     m = oracle.Mesh.from_scenario(s)
-    ho, uo = oracle.fblts(m, oracle.scenario_params(s, split=True), s.level, s.M if M is None else M, s.h0, s.u0,
+    ho, uo = oracle.fblts(m, oracle.scenario_params(s, split=split), s.level, s.M if M is None else M, s.h0, s.u0,
                           s.dt, nsteps)
     dh, du = rel_errors(h, u, ho, uo)
     assert dh <= 1e-10 and du <= 1e-10, (dh, du)
