@@ -10,6 +10,12 @@
 //   edge  : u_s = u0 + c tau Phi(u_in, FB average)
 // Each pass covers the contiguous ranges of its step; the kinetic-energy,
 // vertex and edge-prep (trisk) ranges are derived from what the edge pass reads.
+// With the operator splitting of Sec. 3.2 a slow block (K-only cell pass,
+// vertex pass, TRiSK / edge-prep pass, edge pass writing the slow part of Phi)
+// opens the coarse step, and with its per-fine-step variant (Sec. 4.2) also
+// every fine step; the stages then run only the cell and edge passes.  The
+// classical RK4 comparison scheme is four stages of the same passes on a
+// one-level mesh.
 //
 // Level pair (l, l+1) uses the paper's shrinking sets in the coarse
 // advancement (cells F^5 / F^3 / F^1, edges F_E^4 / F_E^2 / IF-1, plus the
