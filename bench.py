@@ -489,7 +489,7 @@ def run_serve(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=1000, help="timed coarse steps (latency percentiles over them)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fblts", choices=["fblts", "reference"])
     ap.add_argument("--workload", default="basin")

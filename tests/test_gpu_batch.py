@@ -95,3 +95,38 @@ def test_batch_rejects_bad_members():
         fb.batch_create([st32, st32])
     with pytest.raises(fb.FbltsError):
         fb.batch_create([st32], autotune=False, threads_per_block=100)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_mixes_schemes(mode):
+    """Members with the operator splitting (both variants) and RK4 beside a
+    plain FB-LTS member: every launch kind and segment mode goes through the
+    merged kernels, and each member equals its alone run."""
+    bump = scenario.gaussian_bump_case(two_level=True)
+    shelf = scenario.shelf_case(nx=40, ny=32, dc=2e3, M=4, width=10e3, vortex=True)
+    one = np.zeros(bump.mesh.nCells, np.int32)
+    kinds = [dict(s=bump), dict(s=bump, split=1), dict(s=shelf, split=2),
+             dict(s=bump, level=one, M=[], scheme=fb.SCHEME_RK4, dt=bump.dt / 2)]
+
+    def state(k):
+        return make_state(k["s"], level=k.get("level"), M=k.get("M"), precision=fb.FP32_TENDENCY,
+                          split=k.get("split", 0), scheme=k.get("scheme", fb.SCHEME_FBLTS), dt=k.get("dt"))
+
+    n = 8
+    ref = []
+    for k in kinds:
+        st = state(k)
+        fb.lts_advance(st, n)
+        ref.append(fb.state_read(st))
+    states = [state(k) for k in kinds]
+    b = fb.batch_create(states, autotune=False, mode=mode)
+    fb.batch_advance(b, n)
+    fb.batch_synchronize(b)
+    for st, (h0, u0) in zip(states, ref):
+        h, u = fb.state_read(st)
+        if mode == 1:
+            assert np.array_equal(h, h0) and np.array_equal(u, u0)
+        else:
+            dh, du = rel_errors(h, u, h0, u0)
+            assert dh <= 1e-6 and du <= 1e-5, (dh, du)
+    fb.batch_destroy(b)

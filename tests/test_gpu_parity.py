@@ -24,8 +24,9 @@ def _oracle(s, nsteps, M=None, level=None):
 
 
 CASES = {
-    "bump_single": (lambda: scenario.gaussian_bump_case(two_level=False), 100, None),
-    "bump_lts_m2": (lambda: scenario.gaussian_bump_case(two_level=True), 100, None),
+    # the 32x32 bump case for 200 coarse steps, one level and two levels (M=2)
+    "bump_single": (lambda: scenario.gaussian_bump_case(two_level=False), 200, None),
+    "bump_lts_m2": (lambda: scenario.gaussian_bump_case(two_level=True), 200, None),
     "bump_lts_m1": (lambda: scenario.gaussian_bump_case(two_level=True), 30, [1]),
     "bump_lts_m5": (lambda: scenario.gaussian_bump_case(two_level=True), 30, [5]),
     "shelf_forced_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3), 100, None),
