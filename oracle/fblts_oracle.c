@@ -19,8 +19,12 @@
  *     re-evaluated after the fine loop with its substitution rules.
  *     More than two levels: each fine subcycle is itself an FB-LTS step of
  *     the next pair of levels (an extension; the paper treats two levels).
- *   - Classical RK4, used as the reference solution of the convergence
- *     experiment [Sec. 2.3, Fig. convergence].
+ *   - The fast/slow operator splitting [Sec. 3.2, Eq. splitting] and its
+ *     variant with the fine region's slow terms re-evaluated once per fine
+ *     step [proposed at the end of Sec. 4.2].
+ *   - Classical RK4, the reference solution of the convergence experiment
+ *     [Sec. 2.3, Fig. convergence] and the paper's comparison scheme
+ *     [Sec. 4.2, Tab. 2].
  *   - Global diagnostics: total mass and total absolute vorticity.
  *
  * Every value that the scheme has not defined at a given stage is NaN, so a
