@@ -50,8 +50,13 @@ public:
     }
 
     void top(double dt) {
-        if (rk4_) rk4(dt);
-        else step(0, dt, AccInfo{});
+        if (rk4_) {
+            rk4(dt);
+            return;
+        }
+        // the slow part of Phi at the coarse step's start time level on every edge
+        if (split_) slow_block(hm_.nE);
+        step(0, dt, AccInfo{});
     }
 
 private:
@@ -531,28 +536,6 @@ void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool tr
     Op fz;
     fz.kind = OP_FORCING;
     s.ops.push_back(fz);
-    if (split && !rk4) {
-        // the slow part of Phi (Coriolis, kinetic-energy gradient, forcing) at
-        // the coarse step's start time level (h^n, u^n), on every edge
-        // [Sec. 3.2, Eq. splitting]
-        Op k;
-        k.kind = OP_CELL; k.stage = 1; k.in_u = A_U; k.in_h = A_H; k.hst = A_H; k.split = 1;
-        k.seg[0] = Seg{0, hm.nC, SEG_KONLY}; k.nseg = 1; k.lo = 0; k.hi = hm.nC;
-        s.ops.push_back(k);
-        Op v;
-        v.kind = OP_VERT; v.in_u = A_U; v.hst = A_H; v.split = 1;
-        v.seg[0] = Seg{0, hm.nV, SEG_UPD}; v.nseg = 1; v.lo = 0; v.hi = hm.nV;
-        s.ops.push_back(v);
-        Op p;
-        p.kind = trisk_cells ? OP_TRISK : OP_EPREP; p.in_u = A_U; p.hst = A_H; p.split = 1;
-        p.lo = 0; p.hi = trisk_cells ? hm.nC : hm.nE;
-        p.seg[0] = Seg{p.lo, p.hi, SEG_UPD}; p.nseg = 1;
-        s.ops.push_back(p);
-        Op e;
-        e.kind = OP_EDGE; e.in_u = A_U; e.hst = A_H; e.out_u = A_SLOW; e.split = 1;
-        e.seg[0] = Seg{0, hm.nE, SEG_PHI}; e.nseg = 1; e.lo = 0; e.hi = hm.nE;
-        s.ops.push_back(e);
-    }
     Builder b(hm, beta, trisk_cells, rk4 ? 0 : split, rk4, s);
     b.top(dt);
     Op se;
