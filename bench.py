@@ -164,14 +164,17 @@ def oracle_sample(s, budget_s=15.0, threads=1):
     t0 = time.perf_counter()
 
     def run(i):
-        h, u = s.h0.copy(), s.u0.copy()
-        n = 0
-        while True:
-            h, u = oracle.fblts(m, p, s.level, s.M, h, u, s.dt, 1, t0=n * s.dt)
-            n += 1
-            if time.perf_counter() - t0 >= budget_s or n >= 50:
-                break
-        out[i] = (n, h, u)
+        try:
+            h, u = s.h0.copy(), s.u0.copy()
+            n = 0
+            while True:
+                h, u = oracle.fblts(m, p, s.level, s.M, h, u, s.dt, 1, t0=n * s.dt)
+                n += 1
+                if time.perf_counter() - t0 >= budget_s or n >= 50:
+                    break
+            out[i] = (n, h, u)
+        except BaseException as exc:      # re-raised below, in the calling thread
+            out[i] = exc
 
     workers = [threading.Thread(target=run, args=(i,)) for i in range(threads)]
     for w in workers:
@@ -179,6 +182,9 @@ def oracle_sample(s, budget_s=15.0, threads=1):
     for w in workers:
         w.join()
     el = time.perf_counter() - t0
+    for o in out:
+        if isinstance(o, BaseException):
+            raise o
     return sum(o[0] for o in out), el, out[0][1], out[0][2], out[0][0]
 
 
