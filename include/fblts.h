@@ -151,6 +151,25 @@ typedef struct fblts_mesh_info {
 } fblts_mesh_info;
 fblts_status fblts_mesh_get_info(const fblts_mesh *mesh, fblts_mesh_info *info);
 
+/* Region classes of one level pair (Sec. 2.2), host only: validates and
+ * classifies the mesh exactly as fblts_mesh_create does, without touching a
+ * device, and writes per cell and per edge (caller order) the class relative
+ * to the pair (pair, pair + 1):
+ *   FBLTS_REGION_FINE (levels > pair), FBLTS_REGION_IF1, FBLTS_REGION_IF2,
+ *   FBLTS_REGION_INTERIOR (the other cells of level pair),
+ *   FBLTS_REGION_OUTSIDE (levels < pair);
+ * and for fine elements of level pair + 1 the band b of F^b (b = ceil(D/2),
+ * D the cell-layer distance to level pair; 6 when D > 10), for deeper fine
+ * levels 6, else 0.  An edge takes the level of its finest cells, their
+ * smallest distance to the finer level and their smallest band (an edge is in
+ * F_E^b when one of its cells is in F^b).  pair in [0, nLevels - 2], else
+ * FBLTS_E_ARG.  Any output pointer may be NULL; arrays are caller-owned,
+ * nCells resp. nEdges int32. */
+enum { FBLTS_REGION_FINE = 0, FBLTS_REGION_IF1 = 1, FBLTS_REGION_IF2 = 2, FBLTS_REGION_INTERIOR = 3,
+       FBLTS_REGION_OUTSIDE = 4 };
+fblts_status fblts_mesh_regions(const fblts_mesh_desc *desc, int32_t pair, int32_t *cell_class,
+                                int32_t *cell_band, int32_t *edge_class, int32_t *edge_band);
+
 /* ---------------------------------------------------------------------- */
 /* State                                                                   */
 /* ---------------------------------------------------------------------- */

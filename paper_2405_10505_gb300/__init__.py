@@ -20,6 +20,7 @@ from . import build as _build
 
 OK, E_ARG, E_MESH, E_REGIONS, E_OOM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE = range(9)
 FP64, FP32_TENDENCY = 0, 1
+REGION_FINE, REGION_IF1, REGION_IF2, REGION_INTERIOR, REGION_OUTSIDE = range(5)
 SCHEME_FBLTS, SCHEME_RK4 = 0, 1
 FORCE_WIND_STRESS, FORCE_BOTTOM_DRAG, FORCE_VORTEX = 1, 2, 4
 PAPER_BETA = (0.531, 0.531, 0.313)   # Sec. 2.1, CFL-optimised FB weights
@@ -98,7 +99,7 @@ class ServerStats(C.Structure):
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_TAKEN = range(5)
 
 _LIB = None
-SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts_mesh_get_info",
+SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts_mesh_get_info", "fblts_mesh_regions",
            "fblts_state_init", "fblts_state_destroy", "fblts_lts_advance", "fblts_synchronize",
            "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
            "fblts_state_time", "fblts_state_save", "fblts_state_load", "fblts_state_launches_per_step",
@@ -128,6 +129,7 @@ def lib():
             "fblts_mesh_create": [C.POINTER(MeshDesc), C.POINTER(V)],
             "fblts_mesh_destroy": [V],
             "fblts_mesh_get_info": [V, C.POINTER(MeshInfo)],
+            "fblts_mesh_regions": [C.POINTER(MeshDesc), C.c_int32, _PI, _PI, _PI, _PI],
             "fblts_state_init": [V, C.POINTER(Params), _PD, _PD, _PD, C.POINTER(V)],
             "fblts_state_destroy": [V],
             "fblts_lts_advance": [V, C.c_int64],
@@ -227,6 +229,25 @@ class State:
 
 def mesh_create(m, fVertex, level=None, M=None, nIF1=0, nIF2=0):
     """fblts_mesh_create from MPAS-named arrays on ``m`` (any object with those attributes)."""
+    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2)
+    h = C.c_void_p()
+    _check(lib().fblts_mesh_create(C.byref(d), C.byref(h)))
+    return Mesh(h, keep)
+
+
+def mesh_regions(m, fVertex, level, M, pair, nIF1=0, nIF2=0):
+    """fblts_mesh_regions (host only): per cell and per edge, caller order, the
+    region class of the level pair (pair, pair + 1) and the F^b band."""
+    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2)
+    cc = np.empty(int(m.nCells), np.int32)
+    cb = np.empty(int(m.nCells), np.int32)
+    ec = np.empty(int(m.nEdges), np.int32)
+    eb = np.empty(int(m.nEdges), np.int32)
+    _check(lib().fblts_mesh_regions(C.byref(d), int(pair), _p(cc, _PI), _p(cb, _PI), _p(ec, _PI), _p(eb, _PI)))
+    return cc, cb, ec, eb
+
+
+def _mesh_desc(m, fVertex, level, M, nIF1, nIF2):
     keep = {}
 
     def I(name, arr=None):
@@ -263,9 +284,7 @@ def mesh_create(m, fVertex, level=None, M=None, nIF1=0, nIF2=0):
                  D("angleEdge", optional=True), D("xCell", optional=True), D("yCell", optional=True),
                  D("xEdge", optional=True), D("yEdge", optional=True), lev_p, nL, M_p, int(nIF1), int(nIF2))
     keep["desc"] = d
-    h = C.c_void_p()
-    _check(lib().fblts_mesh_create(C.byref(d), C.byref(h)))
-    return Mesh(h, keep)
+    return d, keep
 
 
 def mesh_destroy(mesh):

@@ -226,6 +226,49 @@ extern "C" fblts_status fblts_mesh_destroy(fblts_mesh *m) {
     return FBLTS_OK;
 }
 
+extern "C" fblts_status fblts_mesh_regions(const fblts_mesh_desc *desc, int32_t pair, int32_t *cell_class,
+                                          int32_t *cell_band, int32_t *edge_class, int32_t *edge_band) {
+    if (!desc) { set_error("mesh_regions: desc is NULL"); return FBLTS_E_ARG; }
+    HostMesh hm;
+    const fblts_status st = build_host_mesh(desc, hm);
+    if (st != FBLTS_OK) return st;
+    if (pair < 0 || pair > hm.L - 2) {
+        set_error("mesh_regions: pair %d outside [0, %d]", pair, hm.L - 2);
+        return FBLTS_E_ARG;
+    }
+    // the band key of an element relative to the pair (pair, pair + 1)
+    auto classify = [&](uint32_t key, int32_t &cls, int32_t &band) {
+        const int level = hm.L - 1 - (int)(key >> 16);
+        const int kin = (int)((key >> 8) & 0xff), kout = (int)(key & 0xff);
+        band = 0;
+        if (level > pair + 1) {
+            cls = FBLTS_REGION_FINE;
+            band = 6;
+        } else if (level == pair + 1) {
+            cls = FBLTS_REGION_FINE;
+            band = 6 - kout;
+        } else if (level == pair) {
+            cls = kin <= hm.nIF1 ? FBLTS_REGION_IF1
+                                 : (kin <= hm.nIF1 + hm.nIF2 ? FBLTS_REGION_IF2 : FBLTS_REGION_INTERIOR);
+        } else {
+            cls = FBLTS_REGION_OUTSIDE;
+        }
+    };
+    for (int i = 0; i < hm.nC; ++i) {
+        int32_t c, b;
+        classify(hm.ckey[i], c, b);
+        if (cell_class) cell_class[hm.cell_n2o[i]] = c;
+        if (cell_band) cell_band[hm.cell_n2o[i]] = b;
+    }
+    for (int e = 0; e < hm.nE; ++e) {
+        int32_t c, b;
+        classify(hm.ekey[e], c, b);
+        if (edge_class) edge_class[hm.edge_n2o[e]] = c;
+        if (edge_band) edge_band[hm.edge_n2o[e]] = b;
+    }
+    return FBLTS_OK;
+}
+
 extern "C" fblts_status fblts_mesh_get_info(const fblts_mesh *m, fblts_mesh_info *info) {
     if (!m || !info) { set_error("mesh_get_info: NULL argument"); return FBLTS_E_ARG; }
     std::memset(info, 0, sizeof(*info));
