@@ -511,7 +511,7 @@ def main():
     ap.add_argument("--serve-hours-scale", type=float, default=0.01,
                     help="serve workload: factor on the 1-48 h durations")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="serve workload: HBM budget (GB)")
-    ap.add_argument("--serve-max-active", type=int, default=0,
+    ap.add_argument("--serve-max-active", type=int, default=6,
                     help="serve workload: running requests at once (0 = as many as the budget allows)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other-precision and global FB-RK(3,2) comparison runs")
