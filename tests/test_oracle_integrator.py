@@ -160,3 +160,12 @@ def test_fbrk32_and_rk4_convergence_orders(mode):
     o_rk = np.log2(np.array(errs_rk4[:-1]) / np.array(errs_rk4[1:]))
     assert np.all(np.abs(o_fb - 2) < 0.15), o_fb
     assert np.all(np.abs(o_rk - 4) < 0.2), o_rk
+
+
+def test_bench_rk4_step_ratio_matches_the_oracle_limit(mode):
+    """bench.py puts RK4 at 2 sqrt(2) / (FB-RK(3,2)'s linear limit) times the
+    FB-RK step; its closed-form limit is the one the oracle's mesh run shows."""
+    import bench
+    lim = bench.fbrk32_imag_limit(oracle.BETA)
+    assert lim == pytest.approx(_stability_limit(mode, oracle.BETA), rel=1e-6)
+    assert bench.RK4_IMAG_LIMIT / lim == pytest.approx(0.732, abs=1e-3)
