@@ -289,6 +289,15 @@ fblts_status fblts_state_load(fblts_state *state, const void *buf, size_t len);
  * in `precision` (one arena per state; host only, no device work). */
 fblts_status fblts_state_device_bytes(const fblts_mesh *mesh, int32_t precision, size_t *bytes);
 
+/* The launch list of one coarse step as fblts_state_init would build it for
+ * `desc` and `params`, host only (no device): the number of schedule ops
+ * (kernel launches, counting any empty range), their algorithmic bytes (the
+ * model of fblts_state_step_bytes) and the cell-updates per step.  Checks the
+ * mesh and the scheme/splitting arguments as fblts_mesh_create and
+ * fblts_state_init do.  Any output pointer may be NULL. */
+fblts_status fblts_plan_step(const fblts_mesh_desc *desc, const fblts_params *params, int64_t *ops,
+                             double *alg_bytes, int64_t *cell_updates);
+
 /* Launch statistics of one coarse step: kernels launched per step. */
 fblts_status fblts_state_launches_per_step(const fblts_state *state, int64_t *launches);
 

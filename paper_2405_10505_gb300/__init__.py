@@ -100,6 +100,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_TAKEN = range(5)
 
 _LIB = None
 SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts_mesh_get_info", "fblts_mesh_regions",
+           "fblts_plan_step",
            "fblts_state_init", "fblts_state_destroy", "fblts_lts_advance", "fblts_synchronize",
            "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
            "fblts_state_time", "fblts_state_save", "fblts_state_load", "fblts_state_launches_per_step",
@@ -130,6 +131,8 @@ def lib():
             "fblts_mesh_destroy": [V],
             "fblts_mesh_get_info": [V, C.POINTER(MeshInfo)],
             "fblts_mesh_regions": [C.POINTER(MeshDesc), C.c_int32, _PI, _PI, _PI, _PI],
+            "fblts_plan_step": [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(C.c_int64), _PD,
+                                C.POINTER(C.c_int64)],
             "fblts_state_init": [V, C.POINTER(Params), _PD, _PD, _PD, C.POINTER(V)],
             "fblts_state_destroy": [V],
             "fblts_lts_advance": [V, C.c_int64],
@@ -245,6 +248,16 @@ def mesh_regions(m, fVertex, level, M, pair, nIF1=0, nIF2=0):
     eb = np.empty(int(m.nEdges), np.int32)
     _check(lib().fblts_mesh_regions(C.byref(d), int(pair), _p(cc, _PI), _p(cb, _PI), _p(ec, _PI), _p(eb, _PI)))
     return cc, cb, ec, eb
+
+
+def plan_step(m, fVertex, level, M, params, nIF1=0, nIF2=0):
+    """fblts_plan_step (host only): (launches, algorithmic bytes, cell-updates)
+    of one coarse step for these parameters."""
+    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2)
+    n, cu = C.c_int64(), C.c_int64()
+    b = C.c_double()
+    _check(lib().fblts_plan_step(C.byref(d), C.byref(params), C.byref(n), C.byref(b), C.byref(cu)))
+    return int(n.value), float(b.value), int(cu.value)
 
 
 def _mesh_desc(m, fVertex, level, M, nIF1, nIF2):

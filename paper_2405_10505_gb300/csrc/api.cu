@@ -269,6 +269,37 @@ extern "C" fblts_status fblts_mesh_regions(const fblts_mesh_desc *desc, int32_t 
     return FBLTS_OK;
 }
 
+extern "C" fblts_status fblts_plan_step(const fblts_mesh_desc *desc, const fblts_params *p, int64_t *ops,
+                                       double *alg_bytes, int64_t *cell_updates) {
+    if (!desc || !p) { set_error("plan_step: NULL argument"); return FBLTS_E_ARG; }
+    if (p->precision != FBLTS_FP64 && p->precision != FBLTS_FP32_TENDENCY) {
+        set_error("plan_step: unknown precision %d", p->precision);
+        return FBLTS_E_ARG;
+    }
+    if (p->split < 0 || p->split > 2) { set_error("plan_step: split must be 0, 1 or 2"); return FBLTS_E_ARG; }
+    if (p->scheme != FBLTS_SCHEME_FBLTS && p->scheme != FBLTS_SCHEME_RK4) {
+        set_error("plan_step: unknown scheme %d", p->scheme);
+        return FBLTS_E_ARG;
+    }
+    HostMesh hm;
+    const fblts_status st = build_host_mesh(desc, hm);
+    if (st != FBLTS_OK) return st;
+    if (p->scheme == FBLTS_SCHEME_RK4 && (hm.L != 1 || p->split)) {
+        set_error("plan_step: RK4 needs a one-level mesh and split = 0");
+        return FBLTS_E_ARG;
+    }
+    const bool f32 = p->precision == FBLTS_FP32_TENDENCY;
+    Schedule s;
+    build_schedule(hm, p->dt, p->beta, f32 && hm.rows_canonical, p->split, p->scheme == FBLTS_SCHEME_RK4, s);
+    schedule_bytes(hm, p->forcing, f32, s);
+    double b = 0.0;
+    for (const Op &op : s.ops) b += op.alg_bytes;
+    if (ops) *ops = (int64_t)s.ops.size();
+    if (alg_bytes) *alg_bytes = b;
+    if (cell_updates) *cell_updates = hm.cell_updates_per_step;
+    return FBLTS_OK;
+}
+
 extern "C" fblts_status fblts_mesh_get_info(const fblts_mesh *m, fblts_mesh_info *info) {
     if (!m || !info) { set_error("mesh_get_info: NULL argument"); return FBLTS_E_ARG; }
     std::memset(info, 0, sizeof(*info));
