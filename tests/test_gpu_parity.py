@@ -185,3 +185,24 @@ def test_split_parity_with_oracle(name, split):
                           s.dt, nsteps)
     dh, du = rel_errors(h, u, ho, uo)
     assert dh <= 1e-10 and du <= 1e-10, (dh, du)
+
+
+def test_zero_steps_and_bad_counts():
+    """Advancing 0 coarse steps leaves the state bitwise as it was; a negative
+    count is an argument error that leaves the state usable."""
+    s = scenario.gaussian_bump_case(two_level=True)
+    st = make_state(s)
+    fb.lts_advance(st, 3)
+    h0, u0 = fb.state_read(st)
+    fb.lts_advance(st, 0)
+    h1, u1 = fb.state_read(st)
+    assert np.array_equal(h0, h1) and np.array_equal(u0, u1)
+    with pytest.raises(fb.FbltsError) as e:
+        fb.lts_advance(st, -1)
+    assert e.value.status == fb.E_ARG
+    fb.lts_advance(st, 2)
+    ref = make_state(s)
+    fb.lts_advance(ref, 5)
+    h2, u2 = fb.state_read(st)
+    hr, ur = fb.state_read(ref)
+    assert np.array_equal(h2, hr) and np.array_equal(u2, ur)

@@ -69,3 +69,19 @@ def test_rk4_plan_and_its_checks():
         with pytest.raises(fb.FbltsError) as e:
             fb.plan_step(s.mesh, s.fVertex, level, M, fb.make_params(s.dt, **{"scheme": fb.SCHEME_RK4, **kw}))
         assert e.value.status == fb.E_ARG
+
+
+def test_degenerate_meshes():
+    """One level of a tiny periodic mesh (one FB-RK(3,2) step: 14 launches); an
+    empty mesh and a level array that skips a level are rejected."""
+    s = scenario.gaussian_bump_case(nx=4, ny=4, two_level=False)
+    n, b, cu = fb.plan_step(s.mesh, s.fVertex, s.level, [], fb.make_params(s.dt))
+    assert n == 1 + 12 + 1 and cu == 16 and b > 0
+    d = fb.MeshDesc()
+    import ctypes as C
+    n_ = C.c_int64()
+    assert fb.lib().fblts_plan_step(C.byref(d), C.byref(fb.make_params(1.0)), C.byref(n_), None, None) == fb.E_ARG
+    two = scenario.gaussian_bump_case(two_level=True)
+    skip = two.level * 2          # levels 0 and 2, none on level 1
+    with pytest.raises(fb.FbltsError):
+        fb.plan_step(two.mesh, two.fVertex, skip, [2, 2], fb.make_params(two.dt))
