@@ -317,6 +317,23 @@ enum {
     FBLTS_PK_PREDICT, FBLTS_PK_CORRECT, FBLTS_PK_FORCING, FBLTS_PK_STEP_END, FBLTS_PK_TRISK,
     FBLTS_PROFILE_KINDS
 };
+
+/* One op of the launch list that fblts_plan_step describes, host only: its
+ * kind (FBLTS_PK_*), its stage (1..3; 1..4 under RK4; 0 for kinds other than
+ * the cell, vertex, edge-prep, TRiSK and edge passes) and, for those passes,
+ * the segment mode of every element in caller order (cells for the cell and
+ * TRiSK passes, vertices for the vertex pass, edges for the edge-prep and edge
+ * passes): FBLTS_SEG_NONE where the launch does not touch the element, else
+ * stage value, in-place update of the time level, correction sum set / add
+ * (Eq. if_correction), kinetic energy only, the slow part of Phi (Sec. 3.2),
+ * or the RK4 stage modes.  mode has nCells, nVertices or nEdges bytes (NULL
+ * to skip).  index in [0, ops) of fblts_plan_step, else FBLTS_E_ARG. */
+enum {
+    FBLTS_SEG_NONE = 0, FBLTS_SEG_STAGE, FBLTS_SEG_IN_PLACE, FBLTS_SEG_SUM_SET, FBLTS_SEG_SUM_ADD,
+    FBLTS_SEG_KE_ONLY, FBLTS_SEG_TENDENCY, FBLTS_SEG_RK4_SET, FBLTS_SEG_RK4_ADD2, FBLTS_SEG_RK4_FINAL
+};
+fblts_status fblts_plan_op(const fblts_mesh_desc *desc, const fblts_params *params, int64_t index,
+                           int32_t *kind, int32_t *stage, uint8_t *mode);
 fblts_status fblts_state_profile_step(fblts_state *state, double *ms, int64_t *launches,
                                       double *alg_bytes);
 

@@ -21,6 +21,8 @@ from . import build as _build
 OK, E_ARG, E_MESH, E_REGIONS, E_OOM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_STATE = range(9)
 FP64, FP32_TENDENCY = 0, 1
 REGION_FINE, REGION_IF1, REGION_IF2, REGION_INTERIOR, REGION_OUTSIDE = range(5)
+(SEG_NONE, SEG_STAGE, SEG_IN_PLACE, SEG_SUM_SET, SEG_SUM_ADD, SEG_KE_ONLY, SEG_TENDENCY, SEG_RK4_SET,
+ SEG_RK4_ADD2, SEG_RK4_FINAL) = range(10)
 SCHEME_FBLTS, SCHEME_RK4 = 0, 1
 FORCE_WIND_STRESS, FORCE_BOTTOM_DRAG, FORCE_VORTEX = 1, 2, 4
 PAPER_BETA = (0.531, 0.531, 0.313)   # Sec. 2.1, CFL-optimised FB weights
@@ -100,7 +102,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_TAKEN = range(5)
 
 _LIB = None
 SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts_mesh_get_info", "fblts_mesh_regions",
-           "fblts_plan_step",
+           "fblts_plan_step", "fblts_plan_op",
            "fblts_state_init", "fblts_state_destroy", "fblts_lts_advance", "fblts_synchronize",
            "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
            "fblts_state_time", "fblts_state_save", "fblts_state_load", "fblts_state_launches_per_step",
@@ -133,6 +135,8 @@ def lib():
             "fblts_mesh_regions": [C.POINTER(MeshDesc), C.c_int32, _PI, _PI, _PI, _PI],
             "fblts_plan_step": [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(C.c_int64), _PD,
                                 C.POINTER(C.c_int64)],
+            "fblts_plan_op": [C.POINTER(MeshDesc), C.POINTER(Params), C.c_int64, C.POINTER(C.c_int32),
+                              C.POINTER(C.c_int32), C.POINTER(C.c_uint8)],
             "fblts_state_init": [V, C.POINTER(Params), _PD, _PD, _PD, C.POINTER(V)],
             "fblts_state_destroy": [V],
             "fblts_lts_advance": [V, C.c_int64],
@@ -258,6 +262,21 @@ def plan_step(m, fVertex, level, M, params, nIF1=0, nIF2=0):
     b = C.c_double()
     _check(lib().fblts_plan_step(C.byref(d), C.byref(params), C.byref(n), C.byref(b), C.byref(cu)))
     return int(n.value), float(b.value), int(cu.value)
+
+
+def plan_op(m, fVertex, level, M, params, index, nIF1=0, nIF2=0):
+    """fblts_plan_op (host only): (kind name, stage, per-element segment modes in
+    caller order, or None for kinds that are not passes over cells, vertices or
+    edges) of op ``index`` of the coarse step's launch list."""
+    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2)
+    k, st = C.c_int32(), C.c_int32()
+    buf = np.zeros(max(int(m.nCells), int(m.nEdges), int(m.nVertices)), np.uint8)
+    _check(lib().fblts_plan_op(C.byref(d), C.byref(params), int(index), C.byref(k), C.byref(st),
+                               buf.ctypes.data_as(C.POINTER(C.c_uint8))))
+    name = PROFILE_KINDS[k.value]
+    n = {"cell": m.nCells, "trisk": m.nCells, "vertex": m.nVertices, "edge": m.nEdges,
+         "edge_prep": m.nEdges}.get(name)
+    return name, int(st.value), (buf[: int(n)].copy() if n is not None else None)
 
 
 def _mesh_desc(m, fVertex, level, M, nIF1, nIF2):

@@ -1,5 +1,6 @@
 // C ABI of the FB-LTS library (include/fblts.h): handles, device arenas,
 // the captured coarse step, caller-order I/O, diagnostics and checkpoints.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -269,29 +270,38 @@ extern "C" fblts_status fblts_mesh_regions(const fblts_mesh_desc *desc, int32_t 
     return FBLTS_OK;
 }
 
-extern "C" fblts_status fblts_plan_step(const fblts_mesh_desc *desc, const fblts_params *p, int64_t *ops,
-                                       double *alg_bytes, int64_t *cell_updates) {
-    if (!desc || !p) { set_error("plan_step: NULL argument"); return FBLTS_E_ARG; }
+// The host mesh and the launch list of one coarse step for a description and
+// parameters, with the argument checks of fblts_mesh_create / fblts_state_init.
+static fblts_status plan(const fblts_mesh_desc *desc, const fblts_params *p, const char *who, HostMesh &hm,
+                         Schedule &s) {
+    if (!desc || !p) { set_error("%s: NULL argument", who); return FBLTS_E_ARG; }
     if (p->precision != FBLTS_FP64 && p->precision != FBLTS_FP32_TENDENCY) {
-        set_error("plan_step: unknown precision %d", p->precision);
+        set_error("%s: unknown precision %d", who, p->precision);
         return FBLTS_E_ARG;
     }
-    if (p->split < 0 || p->split > 2) { set_error("plan_step: split must be 0, 1 or 2"); return FBLTS_E_ARG; }
+    if (p->split < 0 || p->split > 2) { set_error("%s: split must be 0, 1 or 2", who); return FBLTS_E_ARG; }
     if (p->scheme != FBLTS_SCHEME_FBLTS && p->scheme != FBLTS_SCHEME_RK4) {
-        set_error("plan_step: unknown scheme %d", p->scheme);
+        set_error("%s: unknown scheme %d", who, p->scheme);
         return FBLTS_E_ARG;
     }
-    HostMesh hm;
     const fblts_status st = build_host_mesh(desc, hm);
     if (st != FBLTS_OK) return st;
     if (p->scheme == FBLTS_SCHEME_RK4 && (hm.L != 1 || p->split)) {
-        set_error("plan_step: RK4 needs a one-level mesh and split = 0");
+        set_error("%s: RK4 needs a one-level mesh and split = 0", who);
         return FBLTS_E_ARG;
     }
     const bool f32 = p->precision == FBLTS_FP32_TENDENCY;
-    Schedule s;
     build_schedule(hm, p->dt, p->beta, f32 && hm.rows_canonical, p->split, p->scheme == FBLTS_SCHEME_RK4, s);
     schedule_bytes(hm, p->forcing, f32, s);
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_plan_step(const fblts_mesh_desc *desc, const fblts_params *p, int64_t *ops,
+                                       double *alg_bytes, int64_t *cell_updates) {
+    HostMesh hm;
+    Schedule s;
+    const fblts_status st = plan(desc, p, "plan_step", hm, s);
+    if (st != FBLTS_OK) return st;
     double b = 0.0;
     for (const Op &op : s.ops) b += op.alg_bytes;
     if (ops) *ops = (int64_t)s.ops.size();
@@ -746,6 +756,43 @@ static int op_kind_profile(int kind) {
         case OP_TRISK: return FBLTS_PK_TRISK;
         default: return FBLTS_PK_STEP_END;
     }
+}
+
+static_assert(FBLTS_SEG_NONE == SEG_NONE && FBLTS_SEG_STAGE == SEG_UPD && FBLTS_SEG_IN_PLACE == SEG_INPLACE &&
+                  FBLTS_SEG_SUM_SET == SEG_ACC_SET && FBLTS_SEG_SUM_ADD == SEG_ACC_ADD &&
+                  FBLTS_SEG_KE_ONLY == SEG_KONLY && FBLTS_SEG_TENDENCY == SEG_PHI && FBLTS_SEG_RK4_SET == SEG_RK_SET &&
+                  FBLTS_SEG_RK4_ADD2 == SEG_RK_ADD2 && FBLTS_SEG_RK4_FINAL == SEG_RK_FIN,
+              "public segment modes");
+
+extern "C" fblts_status fblts_plan_op(const fblts_mesh_desc *desc, const fblts_params *p, int64_t index,
+                                     int32_t *kind, int32_t *stage, uint8_t *mode) {
+    HostMesh hm;
+    Schedule s;
+    const fblts_status st = plan(desc, p, "plan_op", hm, s);
+    if (st != FBLTS_OK) return st;
+    if (index < 0 || index >= (int64_t)s.ops.size()) {
+        set_error("plan_op: index %lld outside [0, %zu)", (long long)index, s.ops.size());
+        return FBLTS_E_ARG;
+    }
+    const Op &op = s.ops[(size_t)index];
+    const bool pass = op.kind == OP_CELL || op.kind == OP_VERT || op.kind == OP_EPREP || op.kind == OP_EDGE ||
+                      op.kind == OP_TRISK;
+    if (kind) *kind = op_kind_profile(op.kind);
+    if (stage) *stage = pass ? op.stage : 0;
+    if (mode && pass) {
+        const bool cells = op.kind == OP_CELL || op.kind == OP_TRISK, verts = op.kind == OP_VERT;
+        const int n = cells ? hm.nC : (verts ? hm.nV : hm.nE);
+        const std::vector<int> &n2o = cells ? hm.cell_n2o : (verts ? hm.vert_n2o : hm.edge_n2o);
+        for (int x = 0; x < n; ++x) mode[n2o[x]] = SEG_NONE;
+        // the last segment containing an element decides its mode, as in the kernels
+        for (int x = std::max(op.lo, 0); x < std::min(op.hi, n); ++x) {
+            int m = SEG_NONE;
+            for (int k = 0; k < op.nseg; ++k)
+                if (x >= op.seg[k].begin && x < op.seg[k].end) m = op.seg[k].mode;
+            mode[n2o[x]] = (uint8_t)m;
+        }
+    }
+    return FBLTS_OK;
 }
 
 extern "C" fblts_status fblts_state_profile_step(fblts_state *s, double *ms, int64_t *launches, double *bytes) {

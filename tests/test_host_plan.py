@@ -85,3 +85,84 @@ def test_degenerate_meshes():
     skip = two.level * 2          # levels 0 and 2, none on level 1
     with pytest.raises(fb.FbltsError):
         fb.plan_step(two.mesh, two.fVertex, skip, [2, 2], fb.make_params(two.dt))
+
+
+def _first_advancement(s, params, after):
+    """Per stage 1..3, the cell and edge modes of the first coarse advancement
+    that starts after op index ``after``."""
+    n, _, _ = fb.plan_step(s.mesh, s.fVertex, s.level, s.M, params)
+    cells, edges, i = {}, {}, after + 1
+    while i < n and (len(cells) < 3 or len(edges) < 3):
+        kind, stage, mode = fb.plan_op(s.mesh, s.fVertex, s.level, s.M, params, i)
+        if kind == "cell" and stage not in cells:
+            cells[stage] = mode
+        if kind == "edge" and stage not in edges and stage in cells:
+            edges[stage] = mode
+        i += 1
+    return cells, edges, i
+
+
+@pytest.mark.parametrize("name", ["bump_m2", "nested_3level", "basin_1_64"])
+def test_coarse_advancement_uses_the_shrinking_sets(name):
+    """The stages of a pair's coarse advancement update exactly the paper's
+    shrinking sets (Sec. 2.2, computed by the oracle): cells F^5, F^3, F^1 and
+    edges F_E^4, F_E^2 plus the coarse region, and in stage 3 the IF-1 and
+    interior edges only (velocity stage 3 is skipped on IF-2 edges)."""
+    s = CASES[name]()
+    import oracle
+    cc, cd, ec, ed, st = oracle.regions(oracle.Mesh.from_scenario(s), s.level)
+    params = fb.make_params(s.dt)
+    after = 0
+    for pair in range(len(s.M)):
+        cells, edges, last = _first_advancement(s, params, after)
+        coarse_c = np.isin(cc[pair], (oracle.RC_IF1, oracle.RC_IF2, oracle.RC_INT))
+        coarse_e = np.isin(ec[pair], (oracle.RC_IF1, oracle.RC_IF2, oracle.RC_INT))
+        fine_c, fine_e = cc[pair] == oracle.RC_FINE, ec[pair] == oracle.RC_FINE
+        want_c = {1: fine_c & (cd[pair] <= 10), 2: fine_c & (cd[pair] <= 6), 3: fine_c & (cd[pair] <= 2)}
+        want_e = {1: (fine_e & (ed[pair] <= 8)) | coarse_e, 2: (fine_e & (ed[pair] <= 4)) | coarse_e,
+                  3: np.isin(ec[pair], (oracle.RC_IF1, oracle.RC_INT))}
+        for k in (1, 2, 3):
+            upd_c = np.isin(cells[k], (fb.SEG_STAGE, fb.SEG_IN_PLACE))
+            upd_e = np.isin(edges[k], (fb.SEG_STAGE, fb.SEG_IN_PLACE))
+            np.testing.assert_array_equal(upd_c, want_c[k] | coarse_c, err_msg=f"pair {pair} cell stage {k}")
+            np.testing.assert_array_equal(upd_e, want_e[k], err_msg=f"pair {pair} edge stage {k}")
+        # interior cells and edges are updated in place by stage 3
+        np.testing.assert_array_equal(cells[3] == fb.SEG_IN_PLACE, cc[pair] == oracle.RC_INT)
+        # the next pair's coarse advancement starts after this pair's first prediction
+        while fb.plan_op(s.mesh, s.fVertex, s.level, s.M, params, last)[0] != "predict":
+            last += 1
+        after = last
+
+
+@pytest.mark.parametrize("name", ["bump_m2", "nested_3level"])
+def test_correction_sums_cover_if1_and_if2(name):
+    """Every launch that accumulates the interface correction (Eq. if_correction)
+    covers exactly IF-1 u IF-2 of one level pair, cells and edges alike; each
+    pair step sets the sums once (k = 0) and adds for k = 1..M-1."""
+    s = CASES[name]()
+    import oracle
+    cc, cd, ec, ed, st = oracle.regions(oracle.Mesh.from_scenario(s), s.level)
+    params = fb.make_params(s.dt)
+    n, _, _ = fb.plan_step(s.mesh, s.fVertex, s.level, s.M, params)
+    sets = {(p, kind): [] for p in range(len(s.M)) for kind in ("cell", "edge")}
+    for i in range(n):
+        kind, stage, mode = fb.plan_op(s.mesh, s.fVertex, s.level, s.M, params, i)
+        if kind not in ("cell", "edge"):
+            continue
+        acc = np.isin(mode, (fb.SEG_SUM_SET, fb.SEG_SUM_ADD))
+        if not acc.any():
+            continue
+        cls = cc if kind == "cell" else ec
+        pairs = [p for p in range(len(s.M)) if np.array_equal(acc, np.isin(cls[p], (oracle.RC_IF1, oracle.RC_IF2)))]
+        assert len(pairs) == 1, (i, kind)
+        assert stage == 3
+        modes = set(np.unique(mode[acc]).tolist())
+        assert len(modes) == 1
+        sets[pairs[0], kind].append(modes.pop())
+    steps = np.cumprod([1] + list(s.M))
+    for p in range(len(s.M)):
+        for kind in ("cell", "edge"):
+            got = sets[p, kind]
+            assert len(got) == steps[p] * s.M[p]
+            assert got.count(fb.SEG_SUM_SET) == steps[p]
+            assert all(got[j] == (fb.SEG_SUM_SET if j % s.M[p] == 0 else fb.SEG_SUM_ADD) for j in range(len(got)))
