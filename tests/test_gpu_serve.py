@@ -83,3 +83,42 @@ def test_server_rejects_what_can_never_fit():
     with pytest.raises(fb.FbltsError):
         fb.server_submit(srv, mesh, _params(s, fb.FP32_TENDENCY), s.h0, s.u0, s.bottom, 3)
     fb.server_destroy(srv)
+
+
+def test_served_split_and_rk4_requests_equal_alone_runs():
+    """Requests with the operator splitting (both variants) and RK4 beside plain
+    ones share the device and each comes out bitwise as its alone run."""
+    bump = scenario.gaussian_bump_case(two_level=True)
+    one = np.zeros(bump.mesh.nCells, np.int32)
+    m2 = fb.mesh_create(bump.mesh, bump.fVertex, level=bump.level, M=bump.M)
+    m1 = fb.mesh_create(bump.mesh, bump.fVertex, level=one, M=[])
+    kinds = [(m2, dict(split=1), 6), (m2, dict(split=2), 5), (m1, dict(scheme=fb.SCHEME_RK4), 7), (m2, {}, 4)]
+
+    def params(kw, precision):
+        p = _params(bump, precision)
+        p.split = kw.get("split", 0)
+        p.scheme = kw.get("scheme", fb.SCHEME_FBLTS)
+        return p
+
+    srv = fb.server_create(hbm_budget=0, steps_per_issue=1)
+    ids, want = [], []
+    for mesh, kw, n in kinds:
+        for precision in (fb.FP64, fb.FP32_TENDENCY):
+            ids.append(fb.server_submit(srv, mesh, params(kw, precision), bump.h0, bump.u0, bump.bottom, n))
+            st = fb.state_init(mesh, params(kw, precision), bump.h0, bump.u0, bump.bottom)
+            fb.lts_advance(st, n)
+            want.append(fb.state_read(st))
+            fb.state_destroy(st)
+    results = {}
+    t0 = time.time()
+    while len(results) < len(ids):
+        assert time.time() - t0 < 120
+        fb.server_progress(srv)
+        for rid in ids:
+            if rid not in results and fb.server_request_info(srv, rid).status == fb.REQ_DONE:
+                results[rid] = fb.server_take(srv, rid)
+    assert fb.server_stats(srv).max_running >= 2
+    for rid, (h0, u0) in zip(ids, want):
+        h, u = results[rid]
+        assert np.array_equal(h, h0) and np.array_equal(u, u0)
+    fb.server_destroy(srv)
