@@ -16,6 +16,13 @@
  *     correction [Eq. if_correction].  More than two levels are handled by
  *     nesting: each fine subcycle of a level pair is an FB-LTS step of the
  *     next pair.
+ *   - optionally with the fast/slow operator splitting [Sec. 3.2] or its
+ *     per-fine-step variant [Sec. 4.2]; for comparison, global FB-RK(3,2) or
+ *     classical RK4 [Sec. 4.2, Tab. 2] on a one-level mesh.
+ *
+ * Groups of calls: mesh (create, info, and the host-only region and launch
+ * planning queries), state (init, advance, I/O, diagnostics, checkpoints,
+ * measurement), allocation-free diagnostics, batched ensemble, serving loop.
  *
  * Conventions common to every call:
  *   - Every function returns an fblts_status; none aborts, traps or exits.
