@@ -220,6 +220,29 @@ def nested_disk_case(nx=48, ny=48, dc=10e3, H=1000.0, f=1e-4, amp=1.0, efold=60e
                     level=level, M=list(M), dt=dt)
 
 
+def three_level_wave_case(nx=48, dc=10e3, H=1000.0, amp=5.0, efold=60e3, r_inner=40e3, sep=8,
+                          M=(2, 2), dt=10.0):
+    """Three LTS levels for a convergence study: a doubly periodic hex mesh
+    with level 2 a disk of radius ``r_inner`` about the centre, level 1 the
+    cells within ``sep`` layers of it (the oracle needs levels 0 and 2 at least
+    7 layers apart), level 0 the rest; f = 0, flat bottom and a Gaussian bump
+    of ``amp`` metres centred on the finest disk, so the gravity wave crosses
+    both interfaces."""
+    mesh = finalize(hex_periodic(nx, nx, dc))
+    Lx, Ly = mesh.period
+    dx = _min_image(mesh.xCell - Lx / 2, Lx)
+    dy = _min_image(mesh.yCell - Ly / 2, Ly)
+    r2 = dx ** 2 + dy ** 2
+    inner = r2 <= r_inner ** 2
+    level = np.zeros(mesh.nCells, np.int32)
+    level[graph_distance(mesh, inner) <= sep] = 1
+    level[inner] = 2
+    h0 = H + amp * np.exp(-r2 / efold ** 2)
+    return Scenario(name=f"three_level_hex{nx}x{nx}", mesh=mesh, bottom=np.full(mesh.nCells, -H),
+                    fVertex=np.zeros(mesh.nVertices), h0=h0, u0=np.zeros(mesh.nEdges), level=level,
+                    M=list(M), dt=dt)
+
+
 def jittered_voronoi_case(k=38, L=300e3, jitter=0.45, H=1000.0, f=1e-4, amp=1.0, efold=40e3,
                           fine_radius=70e3, M=2, seed=3):
     """Irregular Voronoi mesh: a k x k grid of generators in a square box,

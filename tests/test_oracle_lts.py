@@ -11,7 +11,11 @@ Independent facts used:
   shrinking sets changes nothing (bitwise).
 * Appendix A: the predictions reproduce linear-in-time data exactly.
 * Sec. 2.3 / Fig. convergence: second-order convergence against RK4 with
-  M = 4, separately on fine, IF-1, IF-2 and interior cells and edges.
+  M = 4, separately on fine, IF-1, IF-2 and interior cells and edges; and
+  with three levels (M = 2 at both pairs), separately on those sets of both
+  level pairs, which pins the hand-off of the outer pair's IF-1 predictions
+  of subcycle k (Eq. preds) into the inner pair's coarse advancement: a
+  prediction from the wrong subcycle leaves the interface first order.
 * A lake at rest over variable bathymetry stays at rest.
 """
 import numpy as np
@@ -163,6 +167,37 @@ def test_second_order_convergence_per_region():
         h, u = oracle.fblts(m, p, s.level, [4], s.h0, s.u0, dt, int(T / dt))
         errs.append([np.sqrt(np.mean((h - href)[cc[0] == r] ** 2)) for r in range(4)]
                     + [np.sqrt(np.mean((u - uref)[ec[0] == r] ** 2)) for r in range(4)])
+    errs = np.array(errs)
+    orders = np.log2(errs[:-1] / errs[1:])
+    assert np.all(np.abs(orders - 2.0) < 0.1), orders
+
+
+@pytest.mark.slow
+def test_second_order_convergence_three_levels_per_region():
+    """Each fine subcycle of the pair (0, 1) is an FB-LTS step of the pair
+    (1, 2) whose coarse advancement reads the outer IF-1 predictions of that
+    subcycle as boundary data (Sec. 2.2 steps 2-3).  The scheme stays second
+    order (Sec. 2.3) on every set of both pairs only if the subcycle index of
+    those predictions is right; the orders are measured against RK4 on the
+    linear-pressure gravity wave (Eq. grav_wave_model, f = 0)."""
+    s = scenario.three_level_wave_case()
+    m = oracle.Mesh.from_scenario(s)
+    p = oracle.params(terms=oracle.T_PGRAD)
+    T = 1600.0
+    dt_ref = 40.0 / 64
+    href, uref = oracle.rk4(m, p, s.h0, s.u0, dt_ref, int(round(T / dt_ref)))
+    cc, cd, ec, ed, st = oracle.regions(m, s.level)
+    assert st == 0 and cc.shape[0] == 2
+    errs = []
+    for dt in (10.0, 5.0, 2.5):
+        h, u = oracle.fblts(m, p, s.level, s.M, s.h0, s.u0, dt, int(round(T / dt)))
+        row = []
+        for pair in (0, 1):
+            for r in (oracle.RC_FINE, oracle.RC_IF1, oracle.RC_IF2, oracle.RC_INT):
+                assert (cc[pair] == r).any() and (ec[pair] == r).any()
+                row.append(np.sqrt(np.mean((h - href)[cc[pair] == r] ** 2)))
+                row.append(np.sqrt(np.mean((u - uref)[ec[pair] == r] ** 2)))
+        errs.append(row)
     errs = np.array(errs)
     orders = np.log2(errs[:-1] / errs[1:])
     assert np.all(np.abs(orders - 2.0) < 0.1), orders
