@@ -138,6 +138,10 @@ typedef struct fblts_mesh_desc {
  * edges and vertices so that every region is one contiguous range, and
  * uploads the metadata to the current CUDA device.  *out receives the handle. */
 fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mesh **out);
+/* Frees the mesh.  Refused with FBLTS_E_STATE (the mesh stays valid) while a
+ * state created on it is not destroyed or a server request naming it is not
+ * taken and its server not destroyed: all of them read the mesh's device
+ * tables. */
 fblts_status fblts_mesh_destroy(fblts_mesh *mesh);
 
 /* Counts derived by fblts_mesh_create (host only, no device work). */
@@ -356,7 +360,7 @@ fblts_status fblts_state_step_bytes(const fblts_state *state, double *alg_bytes,
  * tight driver loop where cudaMalloc / cudaFree would synchronise the device
  * and stall other work.
  *
- * Computes the same total mass and total absolute vorticity as
+ * Computes the total mass and total absolute vorticity of
  * fblts_diagnostics, from state arrays the caller already holds on the
  * device: d_h[nCells] and d_u[nEdges] in the caller's cell / edge order.  The
  * two results are written to the device array d_out[2] (mass, absolute
@@ -373,6 +377,14 @@ fblts_status fblts_state_step_bytes(const fblts_state *state, double *alg_bytes,
  * it reads (nothing carries over from an earlier call), so calls that
  * overlap on the GPU race: order them on one stream or synchronise between
  * them.  The mesh's device must be current.
+ *
+ * The result is deterministic, but it sums in another order than
+ * fblts_diagnostics (contiguous blocks of 8192 elements against a
+ * grid-stride tree), so the two agree to rounding, not bit for bit: compare
+ * a mass drift between calls of the same entry point.  The looked-up address
+ * belongs to the device's context of that moment; after a cudaDeviceReset
+ * (which also frees every mesh and state of this library) do not use the
+ * library again in the same process.
  */
 fblts_status fblts_diagnostics_static(const fblts_mesh *mesh, const double *d_h, const double *d_u,
                                       double *d_out, void *stream);
@@ -458,8 +470,10 @@ fblts_status fblts_batch_destroy(fblts_batch *batch);
  * on that stream, so the running requests' work overlaps on the GPU, and a
  * request admitted while others run starts without waiting for them.
  * fblts_server_progress does not block: call it in a loop.  The server
- * borrows the meshes and the request's h0, u0, bottom until the request is
- * admitted (request_info status leaves 0).
+ * borrows the request's h0, u0, bottom until the request is admitted
+ * (request_info status leaves 0), and its mesh until the request is taken
+ * (fblts_server_take) or the server destroyed; fblts_mesh_destroy refuses a
+ * mesh that a request still names.
  */
 typedef struct fblts_server fblts_server;
 

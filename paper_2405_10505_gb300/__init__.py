@@ -320,9 +320,12 @@ def _mesh_desc(m, fVertex, level, M, nIF1, nIF2):
 
 
 def mesh_destroy(mesh):
-    h, mesh.handle = mesh.handle, None
+    """fblts_mesh_destroy; raises (and keeps the handle) while states or server
+    requests still use the mesh."""
+    h = mesh.handle
     if h:
         _check(lib().fblts_mesh_destroy(h))
+        mesh.handle = None
 
 
 def mesh_get_info(mesh):

@@ -222,6 +222,11 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
 
 extern "C" fblts_status fblts_mesh_destroy(fblts_mesh *m) {
     if (!m) return FBLTS_OK;
+    const int64_t holds = m->holds.load();
+    if (holds > 0) {
+        set_error("mesh_destroy: %lld states or server requests still use this mesh", (long long)holds);
+        return FBLTS_E_STATE;
+    }
     if (m->dbase) cudaFree(m->dbase);
     delete m;
     return FBLTS_OK;
@@ -366,6 +371,7 @@ extern "C" fblts_status fblts_state_destroy(fblts_state *s) {
     if (s->dbase && s->st) cudaFreeAsync(s->dbase, s->st);
     if (s->st) cudaStreamSynchronize(s->st);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+    if (s->mesh) s->mesh->holds.fetch_sub(1);
     delete s;
     return FBLTS_OK;
 }
@@ -490,6 +496,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     fblts_state *s = new (std::nothrow) fblts_state();
     if (!s) { set_error("state_init: host allocation failed"); return FBLTS_E_OOM; }
     s->mesh = m;
+    m->holds.fetch_add(1);
     s->p = *p;
     const int nC = m->hm.nC;
     if (p->stream) {

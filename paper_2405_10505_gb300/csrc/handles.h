@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -39,6 +40,10 @@ struct fblts_mesh {
     };
     mutable std::mutex cache_mu;
     mutable std::vector<CachedSchedule> sched_cache;
+    // states on this mesh plus server requests that name it and are not yet
+    // taken: fblts_mesh_destroy refuses while any is left, since each of them
+    // reads the mesh's device tables
+    mutable std::atomic<int64_t> holds{0};
 };
 
 struct fblts_state {

@@ -50,8 +50,11 @@ struct fblts_server {
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
 
-// frees the request's device state (its memory returns to the budget)
+// frees the request's device state (its memory returns to the budget) and
+// its hold on the mesh
 static void release(fblts_server *srv, Request &r) {
+    if (r.d.mesh) r.d.mesh->holds.fetch_sub(1);
+    r.d.mesh = nullptr;
     if (r.ev) cudaEventDestroy(r.ev);
     r.ev = nullptr;
     if (r.st) {
@@ -103,6 +106,7 @@ extern "C" fblts_status fblts_server_submit(fblts_server *srv, const fblts_reque
     }
     r.cu_per_step = req->mesh->hm.cell_updates_per_step;
     r.t_submit = srv->now();
+    req->mesh->holds.fetch_add(1);
     const int64_t k = srv->next_id++;
     srv->reqs.emplace(k, r);
     srv->queue.push_back(k);

@@ -130,3 +130,24 @@ def test_batch_mixes_schemes(mode):
             dh, du = rel_errors(h, u, h0, u0)
             assert dh <= 1e-6 and du <= 1e-5, (dh, du)
     fb.batch_destroy(b)
+
+
+def test_batch_members_match_oracle():
+    """Every member of a tuned batch, after 100 rounds (the 13 tuning rounds
+    among them), against the FP64 oracle's FB-LTS run of the same scenario
+    (Sec. 2.2) at the FP32 path's bar: h 1e-6 relative, u 1e-5 of max |u|."""
+    import oracle
+    cases = _members()
+    n = 100
+    states = [make_state(s, precision=fb.FP32_TENDENCY) for s in cases]
+    b = fb.batch_create(states, autotune=True)
+    fb.batch_advance(b, n)
+    fb.batch_synchronize(b)
+    assert fb.batch_info(b).tuned == 1
+    for s, st in zip(cases, states):
+        h, u = fb.state_read(st)
+        ho, uo = oracle.fblts(oracle.Mesh.from_scenario(s), oracle.scenario_params(s), s.level, s.M, s.h0,
+                              s.u0, s.dt, n)
+        dh, du = rel_errors(h, u, ho, uo)
+        assert dh <= 1e-6 and du <= 1e-5, (s.name, dh, du)
+    fb.batch_destroy(b)

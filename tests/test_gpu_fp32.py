@@ -19,10 +19,10 @@ CASES = {
     "bump_single": (lambda: scenario.gaussian_bump_case(two_level=False), 100, None),
     "bump_lts_m2": (lambda: scenario.gaussian_bump_case(two_level=True), 100, None),
     "shelf_forced_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3), 100, None),
-    "nested_3level": (lambda: scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3)), 40, None),
-    "shelf_vortex_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3, vortex=True), 60, None),
+    "nested_3level": (lambda: scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3)), 100, None),
+    "shelf_vortex_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3, vortex=True), 100, None),
     # irregular cells of 3..11 edges (12-slot rows, obtuse triangles), 2 levels
-    "jittered_voronoi_m2": (lambda: scenario.jittered_voronoi_case(), 60, None),
+    "jittered_voronoi_m2": (lambda: scenario.jittered_voronoi_case(), 100, None),
 }
 
 

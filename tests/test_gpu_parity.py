@@ -27,13 +27,13 @@ CASES = {
     # the 32x32 bump case for 200 coarse steps, one level and two levels (M=2)
     "bump_single": (lambda: scenario.gaussian_bump_case(two_level=False), 200, None),
     "bump_lts_m2": (lambda: scenario.gaussian_bump_case(two_level=True), 200, None),
-    "bump_lts_m1": (lambda: scenario.gaussian_bump_case(two_level=True), 30, [1]),
-    "bump_lts_m5": (lambda: scenario.gaussian_bump_case(two_level=True), 30, [5]),
+    "bump_lts_m1": (lambda: scenario.gaussian_bump_case(two_level=True), 100, [1]),
+    "bump_lts_m5": (lambda: scenario.gaussian_bump_case(two_level=True), 100, [5]),
     "shelf_forced_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3), 100, None),
-    "nested_3level": (lambda: scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3)), 40, None),
-    "shelf_vortex_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3, vortex=True), 60, None),
+    "nested_3level": (lambda: scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3)), 100, None),
+    "shelf_vortex_m4": (lambda: scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3, vortex=True), 100, None),
     # irregular cells of 3..11 edges (12-slot rows, obtuse triangles), 2 levels
-    "jittered_voronoi_m2": (lambda: scenario.jittered_voronoi_case(), 60, None),
+    "jittered_voronoi_m2": (lambda: scenario.jittered_voronoi_case(), 100, None),
 }
 
 
@@ -206,3 +206,30 @@ def test_zero_steps_and_bad_counts():
     h2, u2 = fb.state_read(st)
     hr, ur = fb.state_read(ref)
     assert np.array_equal(h2, hr) and np.array_equal(u2, ur)
+
+
+def test_mesh_destroy_refused_while_in_use():
+    """A mesh whose device tables a state or a server request still reads
+    cannot be destroyed (FBLTS_E_STATE, the mesh stays usable); once they are
+    gone it can."""
+    s = scenario.gaussian_bump_case(two_level=True)
+    mesh = fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M)
+    st = make_state(s, mesh=mesh)
+    with pytest.raises(fb.FbltsError) as e:
+        fb.mesh_destroy(mesh)
+    assert e.value.status == fb.E_STATE and mesh.handle
+    fb.lts_advance(st, 3)
+    h, u = fb.state_read(st)
+    ref = make_state(s)
+    fb.lts_advance(ref, 3)
+    hr, ur = fb.state_read(ref)
+    assert np.array_equal(h, hr) and np.array_equal(u, ur)
+    fb.state_destroy(st)
+    srv = fb.server_create()
+    fb.server_submit(srv, mesh, fb.make_params(s.dt, g=s.g), s.h0, s.u0, s.bottom, 2)
+    with pytest.raises(fb.FbltsError) as e:
+        fb.mesh_destroy(mesh)
+    assert e.value.status == fb.E_STATE
+    fb.server_destroy(srv)
+    fb.mesh_destroy(mesh)
+    assert mesh.handle is None

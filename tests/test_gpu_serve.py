@@ -122,3 +122,39 @@ def test_served_split_and_rk4_requests_equal_alone_runs():
         h, u = results[rid]
         assert np.array_equal(h, h0) and np.array_equal(u, u0)
     fb.server_destroy(srv)
+
+
+def test_served_requests_match_oracle():
+    """Served requests of 100 coarse steps in both precisions, overlapping on
+    the device, against the FP64 oracle's FB-LTS run of each scenario
+    (Sec. 2.2): FP64 within 1e-10, FP32 tendencies within 1e-6 (h) and 1e-5
+    (u)."""
+    import oracle
+    from tests.gpu_util import rel_errors
+    cases = [scenario.gaussian_bump_case(two_level=True),
+             scenario.shelf_case(nx=64, ny=48, dc=2e3, M=4, width=10e3, vortex=True),
+             scenario.jittered_voronoi_case(),
+             scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3))]
+    n = 100
+    meshes = [fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M) for s in cases]
+    srv = fb.server_create(hbm_budget=0, max_active=4, steps_per_issue=3)
+    reqs = [(c, p) for c in range(len(cases)) for p in (fb.FP32_TENDENCY, fb.FP64)]
+    ids = [fb.server_submit(srv, meshes[c], _params(cases[c], p), cases[c].h0, cases[c].u0, cases[c].bottom, n)
+           for c, p in reqs]
+    results = {}
+    t0 = time.time()
+    while len(results) < len(ids):
+        assert time.time() - t0 < 300
+        fb.server_progress(srv)
+        for rid in ids:
+            if rid not in results and fb.server_request_info(srv, rid).status == fb.REQ_DONE:
+                results[rid] = fb.server_take(srv, rid)
+    assert fb.server_stats(srv).max_running >= 2
+    ref = {c: oracle.fblts(oracle.Mesh.from_scenario(s), oracle.scenario_params(s), s.level, s.M, s.h0, s.u0,
+                           s.dt, n) for c, s in enumerate(cases)}
+    for rid, (c, p) in zip(ids, reqs):
+        h, u = results[rid]
+        dh, du = rel_errors(h, u, *ref[c])
+        tol_h, tol_u = (1e-10, 1e-10) if p == fb.FP64 else (1e-6, 1e-5)
+        assert dh <= tol_h and du <= tol_u, (cases[c].name, p, dh, du)
+    fb.server_destroy(srv)
