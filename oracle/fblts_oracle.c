@@ -27,6 +27,17 @@
  *     [Sec. 4.2, Tab. 2].
  *   - Global diagnostics: total mass and total absolute vorticity.
  *
+ * State.  The prognostic thickness is carried as the surface elevation
+ * xi = h + b (b = -H, the bottom): every tendency is the same function of
+ * h = xi - b, the pressure gradient g grad(h + b) is g grad(xi) [Eq.
+ * nonlinear_swe], and since b does not change, d xi / dt = d h / dt = Psi and
+ * every stage, average, prediction and correction formula of the scheme is the
+ * same for xi as for h.  Stored this way the state rounds at the precision of
+ * the surface displacement (centimetres) rather than of the full depth (up to
+ * kilometres), so two correct FP64 evaluations that round differently still
+ * agree to far below 1e-10 of the velocity scale over deep water.  The
+ * exported calls take and return h; they convert at entry and exit.
+ *
  * Every value that the scheme has not defined at a given stage is NaN, so a
  * result that consumed data outside the stated sets comes out NaN and the
  * call returns OM_E_NAN.  Sums run in the plain index order of the mesh
@@ -140,22 +151,25 @@ typedef struct {
 
 static int present2(const int *pair) { return pair[0] >= 0 && pair[1] >= 0; }
 
+/* Thickness h_i = xi_i - b_i of cell i from the surface elevation xi. */
+static double om_h(const om_mesh *m, const double *xi, int i) { return xi[i] - m->bottom[i]; }
+
 /* Thickness flux F_e = h_e u_e with h_e the mean of the two cells (zero on
  * no-flow edges).  [Eq. trisk_thickness: F_e(u_e, h)] */
-static double om_flux(const om_mesh *m, const om_params *p, const double *u, const double *h, int e) {
+static double om_flux(const om_mesh *m, const om_params *p, const double *u, const double *xi, int e) {
     const int *ce = m->cellsOnEdge + 2 * e;
     if (!present2(ce)) return 0.0;
     if (p->terms & OM_T_LINEAR_FLUX) return p->H_lin * u[e];
-    return 0.5 * (h[ce[0]] + h[ce[1]]) * u[e];
+    return 0.5 * (om_h(m, xi, ce[0]) + om_h(m, xi, ce[1])) * u[e];
 }
 
 /* Psi_i = -(1/A_i) sum_{e in E_i} n_{e,i} l_e F_e   [Eq. trisk_thickness] */
-static double om_psi_cell(const om_mesh *m, const om_params *p, const double *u, const double *h, int i) {
+static double om_psi_cell(const om_mesh *m, const om_params *p, const double *u, const double *xi, int i) {
     double s = 0.0;
     for (int j = 0; j < m->nEdgesOnCell[i]; ++j) {
         int e = m->edgesOnCell[i * m->maxE + j];
         double n = (m->cellsOnEdge[2 * e] == i) ? 1.0 : -1.0;
-        s += n * m->dvEdge[e] * om_flux(m, p, u, h, e);
+        s += n * m->dvEdge[e] * om_flux(m, p, u, xi, e);
     }
     return -s / m->areaCell[i];
 }
@@ -174,14 +188,14 @@ static double om_ke_cell(const om_mesh *m, const double *u, int i) {
  * zeta_v = (1/A_v) sum_{e in E_v} t_{e,v} d_e u_e with t_{e,v} = -1 when v is
  * the first vertex of e, h_v = (1/A_v) sum kite h_i, q_v = (zeta_v + f_v)/h_v.
  * [Eq. trisk_vorticity and the PV q = eta/h of Sec. 2.3] */
-static void om_vertex(const om_mesh *m, const double *u, const double *h, int v,
+static void om_vertex(const om_mesh *m, const double *u, const double *xi, int v,
                       double *zeta, double *hv, double *q) {
     double av = 0.0, hs = 0.0, cs = 0.0;
     for (int j = 0; j < 3; ++j) {
         int c = m->cellsOnVertex[3 * v + j];
         if (c < 0) continue;
         av += m->kiteAreasOnVertex[3 * v + j];
-        hs += m->kiteAreasOnVertex[3 * v + j] * h[c];
+        hs += m->kiteAreasOnVertex[3 * v + j] * om_h(m, xi, c);
     }
     for (int j = 0; j < 3; ++j) {
         int e = m->edgesOnVertex[3 * v + j];
@@ -199,10 +213,10 @@ static void om_vertex(const om_mesh *m, const double *u, const double *h, int v,
  *           - (K_{c1} - K_{c0})/d_e - g (xi_{c1} - xi_{c0})/d_e   (xi = h + b)
  *           + forcing,
  * q_e = (q_{v0} + q_{v1})/2 and F from (u, h) with h the FB-averaged
- * thickness.  [Eq. nonlinear_swe; Eq. trisk_vorticity for q F_perp;
- * Eq. hurricane_model for the forcing terms] */
+ * thickness (given as its surface elevation xi).  [Eq. nonlinear_swe;
+ * Eq. trisk_vorticity for q F_perp; Eq. hurricane_model for the forcing terms] */
 static double om_phi_edge(const om_mesh *m, const om_params *p, const om_forcing *fz,
-                          const double *u, const double *h, const double *K,
+                          const double *u, const double *xi, const double *K,
                           const double *q, int e) {
     const int *ce = m->cellsOnEdge + 2 * e;
     if (!present2(ce)) return 0.0;
@@ -217,15 +231,15 @@ static double om_phi_edge(const om_mesh *m, const om_params *p, const om_forcing
             int ej = m->edgesOnEdge[e * m->maxE2 + j];
             const int *vj = m->verticesOnEdge + 2 * ej;
             double qj = 0.5 * (q[vj[0]] + q[vj[1]]);
-            s += m->weightsOnEdge[e * m->maxE2 + j] * om_flux(m, p, u, h, ej) * 0.5 * (qe + qj);
+            s += m->weightsOnEdge[e * m->maxE2 + j] * om_flux(m, p, u, xi, ej) * 0.5 * (qe + qj);
         }
         val += s;
     }
     if (p->terms & OM_T_KE) val -= (K[c1] - K[c0]) / dc;
     if (p->terms & OM_T_PGRAD)
-        val -= p->g * ((h[c1] + m->bottom[c1]) - (h[c0] + m->bottom[c0])) / dc;
+        val -= p->g * (xi[c1] - xi[c0]) / dc;
     if ((p->terms & OM_T_FORCING) && fz) {
-        double he = 0.5 * (h[c0] + h[c1]);
+        double he = 0.5 * (om_h(m, xi, c0) + om_h(m, xi, c1));
         double vt = 0.0;
         for (int j = 0; j < m->nEdgesOnEdge[e]; ++j) {
             int ej = m->edgesOnEdge[e * m->maxE2 + j];
@@ -261,19 +275,19 @@ static double om_phi_edge(const om_mesh *m, const om_params *p, const om_forcing
  * the fine step there; coarse edges, the interface correction included, keep
  * the values of t^n.  With more levels this holds per level pair. */
 static double om_phi_stage(const om_mesh *m, const om_params *p, const om_forcing *fz, const double *slow,
-                           const double *u, const double *h, const double *K, const double *q, int e) {
-    if (!slow) return om_phi_edge(m, p, fz, u, h, K, q, e);
+                           const double *u, const double *xi, const double *K, const double *q, int e) {
+    if (!slow) return om_phi_edge(m, p, fz, u, xi, K, q, e);
     om_params pf = *p;
     pf.terms = p->terms & OM_T_PGRAD;
-    return om_phi_edge(m, &pf, NULL, u, h, K, q, e) + slow[e];
+    return om_phi_edge(m, &pf, NULL, u, xi, K, q, e) + slow[e];
 }
 
 static void om_all_K(const om_mesh *m, const double *u, double *K);
-static void om_all_q(const om_mesh *m, const double *u, const double *h, double *q);
+static void om_all_q(const om_mesh *m, const double *u, const double *xi, double *q);
 
 /* Phi_slow(u, h) on every edge (0 on no-flow edges), or NULL without splitting. */
 static double *om_slow_terms(const om_mesh *m, const om_params *p, const om_forcing *fz, const double *u,
-                             const double *h) {
+                             const double *xi) {
     if (!p->split) return NULL;
     om_params ps = *p;
     ps.terms = p->terms & ~OM_T_PGRAD;
@@ -281,8 +295,8 @@ static double *om_slow_terms(const om_mesh *m, const om_params *p, const om_forc
     double *K = (double *)malloc(sizeof(double) * (size_t)(m->nC > 0 ? m->nC : 1));
     double *q = (double *)malloc(sizeof(double) * (size_t)(m->nV > 0 ? m->nV : 1));
     om_all_K(m, u, K);
-    om_all_q(m, u, h, q);
-    for (int e = 0; e < m->nE; ++e) slow[e] = om_phi_edge(m, &ps, fz, u, h, K, q, e);
+    om_all_q(m, u, xi, q);
+    for (int e = 0; e < m->nE; ++e) slow[e] = om_phi_edge(m, &ps, fz, u, xi, K, q, e);
     free(K);
     free(q);
     return slow;
@@ -292,9 +306,19 @@ static double *om_slow_terms(const om_mesh *m, const om_params *p, const om_forc
 static void om_all_K(const om_mesh *m, const double *u, double *K) {
     for (int i = 0; i < m->nC; ++i) K[i] = om_ke_cell(m, u, i);
 }
-static void om_all_q(const om_mesh *m, const double *u, const double *h, double *q) {
+static void om_all_q(const om_mesh *m, const double *u, const double *xi, double *q) {
     double z, hv;
-    for (int v = 0; v < m->nV; ++v) om_vertex(m, u, h, v, &z, &hv, &q[v]);
+    for (int v = 0; v < m->nV; ++v) om_vertex(m, u, xi, v, &z, &hv, &q[v]);
+}
+
+/* surface elevation xi = h + b of a thickness array (a new array), and back */
+static double *om_to_xi(const om_mesh *m, const double *h) {
+    double *xi = (double *)malloc(sizeof(double) * (size_t)(m->nC > 0 ? m->nC : 1));
+    for (int i = 0; i < m->nC; ++i) xi[i] = h[i] + m->bottom[i];
+    return xi;
+}
+static void om_from_xi(const om_mesh *m, const double *xi, double *h) {
+    for (int i = 0; i < m->nC; ++i) h[i] = xi[i] - m->bottom[i];
 }
 
 /* ------------------------------------------------------------------ */
@@ -302,22 +326,27 @@ static void om_all_q(const om_mesh *m, const double *u, const double *h, double 
 /* ------------------------------------------------------------------ */
 
 void om_psi(const om_mesh *m, const om_params *p, const double *u, const double *h, double *out) {
-    for (int i = 0; i < m->nC; ++i) out[i] = om_psi_cell(m, p, u, h, i);
+    double *xi = om_to_xi(m, h);
+    for (int i = 0; i < m->nC; ++i) out[i] = om_psi_cell(m, p, u, xi, i);
+    free(xi);
 }
 
 void om_phi(const om_mesh *m, const om_params *p, const double *windN, const double *windT,
             const double *ps, const double *u, const double *h, double *out) {
     double *K = malloc(sizeof(double) * m->nC), *q = malloc(sizeof(double) * m->nV);
     om_forcing fz = {windN, windT, ps};
+    double *xi = om_to_xi(m, h);
     om_all_K(m, u, K);
-    om_all_q(m, u, h, q);
-    for (int e = 0; e < m->nE; ++e) out[e] = om_phi_edge(m, p, windN ? &fz : NULL, u, h, K, q, e);
-    free(K); free(q);
+    om_all_q(m, u, xi, q);
+    for (int e = 0; e < m->nE; ++e) out[e] = om_phi_edge(m, p, windN ? &fz : NULL, u, xi, K, q, e);
+    free(K); free(q); free(xi);
 }
 
 void om_vertex_fields(const om_mesh *m, const double *u, const double *h,
                       double *zeta, double *hv, double *q) {
-    for (int v = 0; v < m->nV; ++v) om_vertex(m, u, h, v, &zeta[v], &hv[v], &q[v]);
+    double *xi = om_to_xi(m, h);
+    for (int v = 0; v < m->nV; ++v) om_vertex(m, u, xi, v, &zeta[v], &hv[v], &q[v]);
+    free(xi);
 }
 
 void om_ke(const om_mesh *m, const double *u, double *K) { om_all_K(m, u, K); }
@@ -365,7 +394,8 @@ static int om_has_nan(const double *a, int n) {
 
 static double *dalloc(int n) { return (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1)); }
 
-/* One FB-RK(3,2) step on the whole mesh  [Eq. fbrk32]. */
+/* One FB-RK(3,2) step on the whole mesh  [Eq. fbrk32]; h holds the surface
+ * elevation xi. */
 static void om_fbrk32_once(const om_mesh *m, const om_params *p, const om_forcing *fz,
                            double *h, double *u, double dt) {
     int nC = m->nC, nE = m->nE;
@@ -408,18 +438,21 @@ static void om_make_forcing(const om_mesh *m, const om_params *p, double t,
 int om_fbrk32(const om_mesh *m, const om_params *p, double *h, double *u, double dt,
               int nsteps, double t0) {
     double *wn = dalloc(m->nE), *wt = dalloc(m->nE), *ps = dalloc(m->nC);
+    double *xi = om_to_xi(m, h);
     om_forcing fz;
     for (int n = 0; n < nsteps; ++n) {
         om_make_forcing(m, p, t0 + n * dt, wn, wt, ps, &fz);
-        om_fbrk32_once(m, p, (p->terms & OM_T_FORCING) ? &fz : NULL, h, u, dt);
+        om_fbrk32_once(m, p, (p->terms & OM_T_FORCING) ? &fz : NULL, xi, u, dt);
     }
-    free(wn); free(wt); free(ps);
+    om_from_xi(m, xi, h);
+    free(wn); free(wt); free(ps); free(xi);
     return (om_has_nan(h, m->nC) || om_has_nan(u, m->nE)) ? OM_E_NAN : OM_OK;
 }
 
 /* Classical four-stage RK4 on (u, h); tendencies Phi(u, h), Psi(u, h). */
-int om_rk4(const om_mesh *m, const om_params *p, double *h, double *u, double dt, int nsteps, double t0) {
+int om_rk4(const om_mesh *m, const om_params *p, double *h_io, double *u, double dt, int nsteps, double t0) {
     int nC = m->nC, nE = m->nE;
+    double *h = om_to_xi(m, h_io);   /* the surface elevation, advanced below */
     double *kh[4], *ku[4];
     for (int s = 0; s < 4; ++s) { kh[s] = dalloc(nC); ku[s] = dalloc(nE); }
     double *hh = dalloc(nC), *uu = dalloc(nE), *K = dalloc(nC), *q = dalloc(m->nV);
@@ -443,7 +476,9 @@ int om_rk4(const om_mesh *m, const om_params *p, double *h, double *u, double dt
     }
     for (int s = 0; s < 4; ++s) { free(kh[s]); free(ku[s]); }
     free(hh); free(uu); free(K); free(q); free(wn); free(wt); free(ps);
-    return (om_has_nan(h, nC) || om_has_nan(u, nE)) ? OM_E_NAN : OM_OK;
+    om_from_xi(m, h, h_io);
+    free(h);
+    return (om_has_nan(h_io, nC) || om_has_nan(u, nE)) ? OM_E_NAN : OM_OK;
 }
 
 /* ------------------------------------------------------------------ */
@@ -576,6 +611,10 @@ int om_regions_build(const om_mesh *m, const int *level, int L, int nIF1, int nI
 /* ------------------------------------------------------------------ */
 /* FB-LTS  [Sec. 2.2]                                                  */
 /* ------------------------------------------------------------------ */
+
+/* Below, every cell array (h, H0, HS1, ..., the predictions and the boundary
+ * data) holds the surface elevation xi = h + b; om_fblts converts at entry
+ * and exit. */
 
 typedef struct {
     const om_mesh *m;
@@ -896,12 +935,13 @@ static int om_advance(om_ctx *c, int l, double tau, double *h, double *u, const 
  * the time steps of levels l and l+1.  full_band = 0 follows the shrinking
  * sets of Sec. 2.2 literally; 1 computes every coarse sub-stage on all of F^5. */
 int om_fblts(const om_mesh *m, const om_params *p, const int *level, int L, const int *M,
-             int nIF1, int nIF2, int full_band, double *h, double *u, double dt, int nsteps, double t0) {
+             int nIF1, int nIF2, int full_band, double *h_io, double *u, double dt, int nsteps, double t0) {
     if (L < 1) return OM_E_ARG;
     for (int l = 0; l + 1 < L; ++l) if (M[l] < 1) return OM_E_ARG;
     om_regions r;
     int st = om_regions_build_internal(m, level, L, nIF1, nIF2, &r);
     if (st != OM_OK) { om_regions_free(&r); return st; }
+    double *h = om_to_xi(m, h_io);   /* the surface elevation, advanced below */
     double *wn = dalloc(m->nE), *wt = dalloc(m->nE), *ps = dalloc(m->nC);
     om_ctx c = {m, p, NULL, &r, M, full_band, OM_OK, NULL};
     om_forcing fz;
@@ -916,6 +956,8 @@ int om_fblts(const om_mesh *m, const om_params *p, const int *level, int L, cons
     }
     free(wn); free(wt); free(ps);
     om_regions_free(&r);
-    if (c.status == OM_OK && (om_has_nan(h, m->nC) || om_has_nan(u, m->nE))) c.status = OM_E_NAN;
+    om_from_xi(m, h, h_io);
+    free(h);
+    if (c.status == OM_OK && (om_has_nan(h_io, m->nC) || om_has_nan(u, m->nE))) c.status = OM_E_NAN;
     return c.status;
 }
