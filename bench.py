@@ -151,27 +151,29 @@ def oracle_sample(s, budget_s=15.0, threads=1):
 
     The oracle is single-threaded; with threads > 1 one instance per thread
     advances its own copy of the state (the C library runs without the
-    interpreter lock), so the host's cores all work, as replicas.  Returns
-    the steps of all instances, the wall time, and the state and step count
-    of the first instance."""
+    interpreter lock), so the host's cores all work, as replicas.  The step
+    count comes from a one-step probe (none when budget_s <= 0: one step);
+    the timed run then takes all its steps in one oracle call, so the state
+    stays in the oracle's own representation throughout.  Returns the steps
+    of all instances, the wall time of the timed runs, and the state and step
+    count of the first instance."""
     import threading
 
     import oracle
     m = oracle.Mesh.from_scenario(s)
     p = oracle.scenario_params(s)
     oracle.lib()
+    n = 1
+    if budget_s > 0:
+        tp = time.perf_counter()
+        oracle.fblts(m, p, s.level, s.M, s.h0, s.u0, s.dt, 1)
+        n = int(max(1, min(50, budget_s / max(time.perf_counter() - tp, 1e-9))))
     out = [None] * threads
     t0 = time.perf_counter()
 
     def run(i):
         try:
-            h, u = s.h0.copy(), s.u0.copy()
-            n = 0
-            while True:
-                h, u = oracle.fblts(m, p, s.level, s.M, h, u, s.dt, 1, t0=n * s.dt)
-                n += 1
-                if time.perf_counter() - t0 >= budget_s or n >= 50:
-                    break
+            h, u = oracle.fblts(m, p, s.level, s.M, s.h0, s.u0, s.dt, n)
             out[i] = (n, h, u)
         except BaseException as exc:      # re-raised below, in the calling thread
             out[i] = exc
@@ -553,6 +555,7 @@ def main():
     cu = int(info.cell_updates_per_step)
     launches = fb.launches_per_step(st)
     step_bytes, _ = fb.state_step_bytes(st)
+    moved_step = sum(v[1] for v in fb.state_bytes_by_kind(st).values())
 
     fb.lts_advance(st, args.warmup)
     fb.synchronize(st)
@@ -578,10 +581,24 @@ def main():
     ms_step = ms_total / args.steps
     value = replica_value(world, cu, args.steps, ms_total)
 
+    # latency percentiles over a window of at least 1000 coarse steps (after the
+    # timed region, whatever --steps is), one event pair per step
+    n_lat = max(1000, args.steps)
+    if n_lat > args.steps:
+        levs = [torch.cuda.Event(enable_timing=True) for _ in range(n_lat + 1)]
+        levs[0].record(stream)
+        for k in range(n_lat):
+            fb.lts_advance(st, 1)
+            levs[k + 1].record(stream)
+        fb.synchronize(st)
+        lat = sorted(levs[k].elapsed_time(levs[k + 1]) for k in range(n_lat))
+
     # per-kernel profile (launch by launch with events on the same stream)
     prof = fb.state_profile_step(st)
+    bykind = fb.state_bytes_by_kind(st)
     dom = max(prof, key=lambda k: prof[k][0])
     dms, dn, dbytes = prof[dom]
+    dmoved = bykind[dom][1]
     hbm, peak_src = peaks()
     achieved = dbytes / (dms / 1000.0) / 1e9
     kernel_name = {"cell": "cell_pass", "vertex": "vert_pass", "edge_prep": "eprep_pass",
@@ -614,12 +631,19 @@ def main():
                    "cell_updates_per_step": cu, "precision": args.precision,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2: {step_bytes / 1e6:.0f} MB algorithmic traffic per step"},
-        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "steps": len(lat)},
         "alg_bytes_per_step": step_bytes,
         "alg_bytes_per_cell_update": step_bytes / cu,
+        "moved_bytes_per_step": moved_step,
         "step_hbm_frac": step_bytes / (ms_step / 1000.0) / 1e9 / hbm,
+        "step_moved_frac": moved_step / (ms_step / 1000.0) / 1e9 / hbm,
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
+                     "alg_bytes_per_launch": dbytes / max(dn, 1), "moved_bytes_per_launch": dmoved / max(dn, 1),
+                     "moved_frac": dmoved / (dms / 1000.0) / 1e9 / hbm,
+                     "moved_over_alg": dmoved / dbytes if dbytes else None,
+                     "traffic_over_alg": (traffic / (dbytes / max(dn, 1))) if (traffic and dbytes) else None,
                      "launches_per_step": dn, "share_of_step": dms / sum(v[0] for v in prof.values())},
         "profile_ms_per_step": {k: round(v[0], 4) for k, v in prof.items()},
         "gpu_launches": int(launches * args.steps + 1),

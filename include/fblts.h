@@ -318,7 +318,8 @@ fblts_status fblts_state_launches_per_step(const fblts_state *state, int64_t *la
  * For each kind k (FBLTS_PK_*), ms[k] is the summed device time, launches[k]
  * the launch count and alg_bytes[k] the algorithmic bytes: every array element
  * the launch's arithmetic must read or write, counted once at its storage
- * size (metadata included).  Arrays have FBLTS_PROFILE_KINDS entries; any may
+ * size (metadata included, at its real length; see
+ * fblts_state_bytes_by_kind).  Arrays have FBLTS_PROFILE_KINDS entries; any may
  * be NULL.  Synchronises.  FBLTS_PK_TRISK is the FP32 path's cell-side TRiSK
  * pass, which replaces the edge prep on meshes whose neighbour lists and
  * weights are the cells' edge rows and kite-fraction weights (mesh_info flags
@@ -352,6 +353,23 @@ fblts_status fblts_state_profile_step(fblts_state *state, double *ms, int64_t *l
  * fblts_state_profile_step) and cell-updates per step. */
 fblts_status fblts_state_step_bytes(const fblts_state *state, double *alg_bytes,
                                     int64_t *cell_updates);
+
+/* Bytes of one coarse step per kind (FBLTS_PROFILE_KINDS entries each; either
+ * pointer may be NULL), host only:
+ *   alg[k]   - algorithmic: every array the stage's arithmetic needs (Eq.
+ *              trisk_thickness, Eq. trisk_vorticity, Eq. fbrk32: state, stage
+ *              values, the intermediates K, q, h*, F, and the mesh metadata),
+ *              each element once per launch at its storage size, metadata at
+ *              its real length (no row or record padding) with the metric
+ *              factors per edge and per cell; the same model as
+ *              fblts_state_step_bytes and fblts_state_profile_step;
+ *   moved[k] - what this library's kernels read and write in their layout:
+ *              padded rows, 16-byte records, per-slot coefficients, and the
+ *              per-slot shares that the FP32 path's TRiSK pass writes and its
+ *              edge pass reads.
+ * moved / alg is the layout's overhead; DRAM traffic above moved means
+ * re-reads that the caches did not catch. */
+fblts_status fblts_state_bytes_by_kind(const fblts_state *state, double *alg, double *moved);
 
 /*
  * Allocation-free global diagnostics.  The paper has no counterpart: this is

@@ -106,7 +106,8 @@ SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts
            "fblts_state_init", "fblts_state_destroy", "fblts_lts_advance", "fblts_synchronize",
            "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
            "fblts_state_time", "fblts_state_save", "fblts_state_load", "fblts_state_launches_per_step",
-           "fblts_state_profile_step", "fblts_state_step_bytes", "fblts_diagnostics_static",
+           "fblts_state_profile_step", "fblts_state_step_bytes", "fblts_state_bytes_by_kind",
+           "fblts_diagnostics_static",
            "fblts_state_device_bytes", "fblts_batch_create", "fblts_batch_advance", "fblts_batch_synchronize", "fblts_batch_get_info",
            "fblts_batch_destroy", "fblts_server_create", "fblts_server_submit", "fblts_server_progress",
            "fblts_server_request_info", "fblts_server_take", "fblts_server_get_stats", "fblts_server_destroy")
@@ -151,6 +152,7 @@ def lib():
             "fblts_state_launches_per_step": [V, C.POINTER(C.c_int64)],
             "fblts_state_profile_step": [V, _PD, C.POINTER(C.c_int64), _PD],
             "fblts_state_step_bytes": [V, _PD, C.POINTER(C.c_int64)],
+            "fblts_state_bytes_by_kind": [V, _PD, _PD],
             "fblts_diagnostics_static": [V, V, V, V, V],
             "fblts_state_device_bytes": [V, C.c_int32, C.POINTER(C.c_size_t)],
             "fblts_batch_create": [C.POINTER(V), C.c_int32, C.POINTER(BatchOpts), C.POINTER(V)],
@@ -446,6 +448,15 @@ def state_step_bytes(state):
     b, cu = C.c_double(), C.c_int64()
     _check(lib().fblts_state_step_bytes(state.handle, C.byref(b), C.byref(cu)))
     return b.value, cu.value
+
+
+def state_bytes_by_kind(state):
+    """Per-kind (algorithmic bytes, moved bytes) of one coarse step."""
+    k = len(PROFILE_KINDS)
+    alg = (C.c_double * k)()
+    moved = (C.c_double * k)()
+    _check(lib().fblts_state_bytes_by_kind(state.handle, alg, moved))
+    return {PROFILE_KINDS[i]: (alg[i], moved[i]) for i in range(k)}
 
 
 def diagnostics_static(mesh, d_h, d_u, d_out, stream=None):

@@ -379,9 +379,9 @@ extern "C" fblts_status fblts_state_destroy(fblts_state *s) {
 static fblts_status upload_state(fblts_state *s, const double *h, const double *u) {
     const fblts_mesh *m = s->mesh;
     const int nC = m->hm.nC, nE = m->hm.nE;
-    if (h) {
+    if (h) {   // the time level holds the surface elevation xi = h + b
         CK(cudaMemcpyAsync(s->d_stage_c, h, sizeof(double) * nC, cudaMemcpyHostToDevice, s->st));
-        CK(launch_gather(s->arr.a[A_H], s->d_stage_c, m->cell_n2o, nC, s->st));
+        CK(launch_gather(s->arr.a[A_H], s->d_stage_c, m->cell_n2o, nC, s->st, s->dm.bottom, +1));
     }
     if (u) {
         CK(cudaMemcpyAsync(s->d_stage_e, u, sizeof(double) * nE, cudaMemcpyHostToDevice, s->st));
@@ -411,6 +411,7 @@ static std::vector<size_t> state_plan(const fblts_mesh *m, bool f32) {
     for (int a = 0; a < A_COUNT; ++a) plan.push_back(count(a) * (is_double(a) ? 8 : 4));
     plan.push_back(szc);                                           // bottom
     plan.push_back(sze); plan.push_back(sze); plan.push_back(sze); plan.push_back(szc);  // forcing (double)
+    if (!f32) { plan.push_back(sze); plan.push_back(sizeof(double) * nV); }   // H_e, H_v
     if (f32) {
         plan.push_back(4 * nC); plan.push_back(4 * nE);            // shadows
         plan.push_back(4 * nE);                                    // H_e
@@ -552,6 +553,11 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     s->fz.windT = (double *)got[gi++];
     s->fz.cw = (double *)got[gi++];
     s->fz.ps = (double *)got[gi++];
+    double *He64 = nullptr, *Hv64 = nullptr;
+    if (!f32) {
+        He64 = (double *)got[gi++];
+        Hv64 = (double *)got[gi++];
+    }
     float *He32 = nullptr;
     float4 *estat = nullptr, *vkh = nullptr;
     if (f32) {
@@ -576,14 +582,21 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     }
     s->dm = m->dm;
     s->dm.bottom = db;
-    fblts_status st = upload_state(s, h0, u0);
-    if (st == FBLTS_OK) {
-        if (cudaMemcpyAsync(s->d_stage_c, bottom, szc, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
-            launch_gather(db, s->d_stage_c, m->cell_n2o, nC, s->st) != cudaSuccess) {
-            set_error("state_init: bottom upload failed");
+    fblts_status st = FBLTS_OK;
+    // the bottom first: the time level is stored as xi = h + b
+    if (cudaMemcpyAsync(s->d_stage_c, bottom, szc, cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
+        launch_gather(db, s->d_stage_c, m->cell_n2o, nC, s->st) != cudaSuccess) {
+        set_error("state_init: bottom upload failed");
+        st = FBLTS_E_CUDA;
+    }
+    if (st == FBLTS_OK && !f32) {
+        s->dm.He64 = He64; s->dm.Hv64 = Hv64;
+        if (launch_fp64_depths(s->dm, He64, Hv64, s->st) != cudaSuccess) {
+            set_error("state_init: FP64 setup failed");
             st = FBLTS_E_CUDA;
         }
     }
+    if (st == FBLTS_OK) st = upload_state(s, h0, u0);
     if (st == FBLTS_OK && f32) {
         s->dm.He32 = He32; s->dm.estat = estat; s->dm.vKh = vkh;
         if (launch_fp32_depths(s->dm, He32, estat, vkh, s->st) != cudaSuccess ||
@@ -620,7 +633,9 @@ extern "C" fblts_status fblts_lts_advance(fblts_state *s, int64_t n) {
         fblts_status st = issue_step(s);
         if (st != FBLTS_OK) return st;
     }
-    if (n > 0) CK(launch_check(s->arr.a[A_H], s->mesh->hm.nC, s->arr.a[A_U], s->mesh->hm.nE, s->d_flag, s->st));
+    if (n > 0)
+        CK(launch_check(s->arr.a[A_H], s->dm.bottom, s->mesh->hm.nC, s->arr.a[A_U], s->mesh->hm.nE, s->d_flag,
+                        s->st));
     s->steps += n;
     return FBLTS_OK;
 }
@@ -645,8 +660,8 @@ extern "C" fblts_status fblts_state_read(const fblts_state *s, double *h_out, do
     if (!s) { set_error("state_read: NULL state"); return FBLTS_E_ARG; }
     const fblts_mesh *m = s->mesh;
     const int nC = m->hm.nC, nE = m->hm.nE;
-    if (h_out) {
-        CK(launch_gather(s->d_stage_c, s->arr.a[A_H], m->cell_o2n, nC, s->st));
+    if (h_out) {   // h = xi - b
+        CK(launch_gather(s->d_stage_c, s->arr.a[A_H], m->cell_o2n, nC, s->st, s->dm.bottom, -1));
         CK(cudaMemcpyAsync(h_out, s->d_stage_c, sizeof(double) * nC, cudaMemcpyDeviceToHost, s->st));
     }
     if (u_out) {
@@ -851,5 +866,21 @@ extern "C" fblts_status fblts_state_step_bytes(const fblts_state *s, double *byt
     for (const Op &op : s->sched.ops) b += op.alg_bytes;
     if (bytes) *bytes = b;
     if (cell_updates) *cell_updates = s->mesh->hm.cell_updates_per_step;
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_state_bytes_by_kind(const fblts_state *s, double *alg, double *moved) {
+    if (!s) { set_error("bytes_by_kind: NULL state"); return FBLTS_E_ARG; }
+    double a[FBLTS_PROFILE_KINDS] = {0}, m[FBLTS_PROFILE_KINDS] = {0};
+    for (const Op &op : s->sched.ops) {
+        if (!op_launches(s, op)) continue;
+        const int k = op_kind_profile(op.kind);
+        a[k] += op.alg_bytes;
+        m[k] += op.moved_bytes;
+    }
+    for (int k = 0; k < FBLTS_PROFILE_KINDS; ++k) {
+        if (alg) alg[k] = a[k];
+        if (moved) moved[k] = m[k];
+    }
     return FBLTS_OK;
 }

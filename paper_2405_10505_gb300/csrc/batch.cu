@@ -542,7 +542,8 @@ extern "C" fblts_status fblts_batch_advance(fblts_batch *b, int64_t n) {
         }
     }
     for (fblts_state *s : b->members) {
-        CK(launch_check(s->arr.a[A_H], s->mesh->hm.nC, s->arr.a[A_U], s->mesh->hm.nE, s->d_flag, b->st));
+        CK(launch_check(s->arr.a[A_H], s->dm.bottom, s->mesh->hm.nC, s->arr.a[A_U], s->mesh->hm.nE, s->d_flag,
+                        b->st));
         s->steps += n;
     }
     b->rounds += n;

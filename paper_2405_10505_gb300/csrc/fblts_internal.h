@@ -146,6 +146,7 @@ struct Op {
     // the time level (no gravity term), 2 = edge stage with Phi = fast + slow
     int split = 0;
     double alg_bytes = 0.0;           // algorithmic bytes of the launch (see op_bytes)
+    double moved_bytes = 0.0;         // bytes its kernel moves in this layout (see op_bytes)
 };
 
 struct Schedule {
@@ -164,7 +165,8 @@ struct Schedule {
 // of an FB-LTS coarse step (beta and split unused)
 void build_schedule(const HostMesh &hm, double dt, const double beta[3], bool trisk_cells, int split, bool rk4,
                     Schedule &s);
-// fills Op::alg_bytes of every op (forcing: the edge passes read the forcing fields)
+// fills Op::alg_bytes and Op::moved_bytes of every op (forcing: the edge
+// passes read the forcing fields)
 void schedule_bytes(const HostMesh &hm, int forcing_flags, bool fp32, Schedule &s);
 
 }  // namespace fblts

@@ -125,9 +125,10 @@ inline IfArgs if_args(const Op &op, const DevArrays &arr) {
 // ---------------------------------------------------------------- bodies
 
 // Cell i: Psi_i = sum_j cDiv_ij h_e u_e (Eq. trisk_thickness with
-// cDiv = -n_{e,i} l_e / A_i and h_e the mean of the two cells), the stage
-// update h_s = h0 + c tau Psi (Eq. fbrk32), its FB average and the kinetic
-// energy K_i = sum_j cKE_ij u_e^2 (cKE = d_e l_e / (4 A_i)).
+// cDiv = -n_{e,i} l_e / A_i and h_e = H_e + (xi_i + xi_nb)/2 the mean of the
+// two cells), the stage update xi_s = xi0 + c tau Psi (Eq. fbrk32), its FB
+// average and the kinetic energy K_i = sum_j cKE_ij u_e^2
+// (cKE = d_e l_e / (4 A_i)).  Thickness arrays hold xi = h - H.
 FB_HD void cell_body(const DevMesh &m, const CellArgs &a, int i) {
     const int mode = seg_mode(a.segs, i);
     if (mode == SEG_NONE) return;
@@ -141,7 +142,7 @@ FB_HD void cell_body(const DevMesh &m, const CellArgs &a, int i) {
         ke += m.cKE[j * nC + i] * ue * ue;
         if (mode != SEG_KONLY) {
             const int nb = m.coc[j * nC + i];
-            psi += (0.5 * m.cDiv[j * nC + i]) * ((hi_ + a.h_in[nb]) * ue);
+            psi += m.cDiv[j * nC + i] * ((m.He64[e] + 0.5 * (hi_ + a.h_in[nb])) * ue);
         }
     }
     a.K[i] = ke;
@@ -178,11 +179,11 @@ FB_HD void cell_body(const DevMesh &m, const CellArgs &a, int i) {
     }
 }
 
-// Vertex v: zeta_v = sum_j t_{e,v} d_e u_e / A_v, h_v = sum_j kite h / A_v,
+// Vertex v: zeta_v = sum_j t_{e,v} d_e u_e / A_v, h_v = H_v + sum_j kite xi / A_v,
 // q_v = (zeta_v + f_v) / h_v  (Eq. trisk_vorticity; PV q = eta / h).
 FB_HD void vert_body(const DevMesh &m, const VertArgs &a, int v) {
     const int nV = m.nV;
-    double z = 0.0, hv = 0.0;
+    double z = 0.0, hv = m.Hv64[v];
 FB_UNROLL
     for (int j = 0; j < 3; ++j) {
         z += m.cVort[j * nV + v] * a.u_in[m.eov[j * nV + v]];
@@ -191,11 +192,12 @@ FB_UNROLL
     a.q[v] = (z + m.fV[v]) / hv;
 }
 
-// Edge e: thickness flux F_e = h_e u_e (zero on no-flow edges), the edge PV
-// q_e = (q_v0 + q_v1) / 2 and their product F_e q_e.
+// Edge e: thickness flux F_e = h_e u_e with h_e = H_e + (xi_c0 + xi_c1)/2
+// (zero on no-flow edges), the edge PV q_e = (q_v0 + q_v1) / 2 and their
+// product F_e q_e.
 FB_HD void prep_body(const DevMesh &m, const PrepArgs &a, int e) {
     const int c0 = m.coe0[e], c1 = m.coe1[e];
-    const double F = m.ebnd[e] ? 0.0 : 0.5 * (a.hst[c0] + a.hst[c1]) * a.u_in[e];
+    const double F = m.ebnd[e] ? 0.0 : (m.He64[e] + 0.5 * (a.hst[c0] + a.hst[c1])) * a.u_in[e];
     const double q = 0.5 * (a.q[m.voe0[e]] + a.q[m.voe1[e]]);
     a.Fe[e] = F;
     a.qe[e] = q;
@@ -204,6 +206,7 @@ FB_HD void prep_body(const DevMesh &m, const PrepArgs &a, int e) {
 
 // Edge e: Phi_e = sum_j w_j F_{e_j} (q_e + q_{e_j}) / 2
 //                 - [K_c1 - K_c0 + g (xi_c1 - xi_c0)] / d_e  (+ forcing)
+// with xi = h + b the stored surface elevation and h_e = H_e + (xi_c0 + xi_c1)/2
 // (rotating SWE, Eq. nonlinear_swe, in TRiSK form; forcing of Eq.
 // hurricane_model), then the stage update u_s = u0 + c tau Phi or the
 // correction sum of Eq. if_correction.  The Coriolis sum is taken as
@@ -217,7 +220,7 @@ FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, 
         // operator splitting [Sec. 3.2, Eq. splitting]: the gravity-wave term at the
         // stage state plus the slow terms of the coarse step
         const int c0 = m.coe0[e], c1 = m.coe1[e];
-        phi = a.slow[e] - a.g * ((a.hst[c1] + m.bottom[c1]) - (a.hst[c0] + m.bottom[c0])) * m.invDc[e];
+        phi = a.slow[e] - a.g * (a.hst[c1] - a.hst[c0]) * m.invDc[e];
     } else if (!m.ebnd[e]) {
         const int nE = m.nE;
         const int c0 = m.coe0[e], c1 = m.coe1[e];
@@ -234,11 +237,11 @@ FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, 
         const double cor = 0.5 * (qself * sF + sG);
         const double h0c = a.hst[c0], h1c = a.hst[c1];
         const double gg = a.split == 1 ? 0.0 : a.g;   // the slow terms leave gravity out
-        const double grad = (a.K[c1] - a.K[c0]) + gg * ((h1c + m.bottom[c1]) - (h0c + m.bottom[c0]));
+        const double grad = (a.K[c1] - a.K[c0]) + gg * (h1c - h0c);
         phi = cor - grad * m.invDc[e];
         if (FORCING) {
             const double ue = a.u_in[e];
-            const double rhe = 2.0 / (h0c + h1c);
+            const double rhe = 1.0 / (m.He64[e] + 0.5 * (h0c + h1c));
             if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
                 const double dn = fz.windN[e] - ue, dt = fz.windT[e] - vt;
                 phi += fz.cw[e] * sqrt(dn * dn + dt * dt) * dn * rhe;

@@ -12,8 +12,7 @@ struct CellArgs32 {
     int lo, hi;
     const float *u_in, *xi_in, *xi0, *xiprev;   // stage inputs, xi of h0, stage-2 xi
     float *xi_out, *xi_shadow, *hst_out, *K;
-    double *h_state, *acc;
-    const double *bottom;
+    double *h_state, *acc;      // the double time level (xi) and the correction sums
     double cdt;
     float fb_a, fb_b, fb_c;
 };
@@ -61,7 +60,6 @@ struct EdgeArgs32 {
 struct IfArgs32 {
     int c_lo, c_if1_hi, c_if12_hi, e_lo, e_if1_hi, e_if12_hi, n;
     double *h, *u, *sh0, *su0, *acch, *accu;
-    const double *bottom;
     float *xi, *u32, *hs1, *hs2, *hs3, *hst1, *hst2, *hst3, *us1, *us2, *us3;
     float *sh1, *sh2, *sh3, *su1, *su2, *su3;
     int k, M;
@@ -83,7 +81,7 @@ inline CellArgs32 cell_args32(const Op &op, const DevArrays &arr, const DevMesh 
     a.u_in = f_in(arr, op.in_u); a.xi_in = f_in(arr, op.in_h); a.xi0 = f_in(arr, op.h0);
     a.xiprev = f_in(arr, op.hprev);
     a.xi_out = arr.f[op.out_h]; a.xi_shadow = arr.xi32; a.hst_out = arr.f[op.hst]; a.K = arr.f[A_K];
-    a.h_state = arr.a[A_H]; a.acc = arr.a[A_ACCH]; a.bottom = m.bottom;
+    a.h_state = arr.a[A_H]; a.acc = arr.a[A_ACCH];
     a.cdt = op.cdt; a.fb_a = (float)op.fb_a; a.fb_b = (float)op.fb_b; a.fb_c = (float)op.fb_c;
     return a;
 }
@@ -123,7 +121,7 @@ inline IfArgs32 if_args32(const Op &op, const DevArrays &arr, const DevMesh &m) 
     a.e_lo = op.e_if1_lo; a.e_if1_hi = op.e_if1_hi; a.e_if12_hi = op.e_if12_hi;
     a.n = op.hi;
     a.h = arr.a[A_H]; a.u = arr.a[A_U]; a.sh0 = arr.a[A_SH0]; a.su0 = arr.a[A_SU0];
-    a.acch = arr.a[A_ACCH]; a.accu = arr.a[A_ACCU]; a.bottom = m.bottom;
+    a.acch = arr.a[A_ACCH]; a.accu = arr.a[A_ACCU];
     a.xi = arr.xi32; a.u32 = arr.u32;
     a.hs1 = arr.f[A_HS1]; a.hs2 = arr.f[A_HS2]; a.hs3 = arr.f[A_HS3];
     a.hst1 = arr.f[A_HST1]; a.hst2 = arr.f[A_HST2]; a.hst3 = arr.f[A_HST3];
@@ -237,7 +235,7 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
         case SEG_INPLACE: {
             const float x0 = a.xi0[i];
             const double hn = a.h_state[i] + a.cdt * psi;
-            const float xn = (float)(hn + a.bottom[i]);
+            const float xn = (float)hn;
             a.h_state[i] = hn;
             a.xi_shadow[i] = xn;
             const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;   // the stage-2 value enters stage 3 only
@@ -250,7 +248,7 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
         case SEG_RK_FIN: {
             const float x0 = a.xi0[i];
             const double hn = a.h_state[i] + a.cdt * (a.acc[i] + psi);
-            const float xn = (float)(hn + a.bottom[i]);
+            const float xn = (float)hn;
             a.h_state[i] = hn;
             a.xi_shadow[i] = xn;
             const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;
@@ -491,7 +489,7 @@ FB_HD void pred32_body(const IfArgs32 &a, int t) {
     const float wk = a.k / Md, wk1 = (a.k + 1) / Md, w1 = 1.f / Md;
     const int i = a.c_lo + t;
     if (i < a.c_if1_hi) {
-        const float x0 = (float)(a.sh0[i] + a.bottom[i]);
+        const float x0 = (float)a.sh0[i];
         const float x13 = a.sh1[i], x12 = a.sh2[i], x1 = a.sh3[i];
         const float hk = wk * x1 + (1.f - wk) * x0;
         const float hk1 = wk1 * x1 + (1.f - wk1) * x0;
@@ -519,7 +517,7 @@ FB_HD void final32_body(const IfArgs32 &a, const unsigned char *ebnd, int t) {
     if (i < a.c_if12_hi) {
         const double hn = a.sh0[i] + a.cf * a.acch[i];
         a.h[i] = hn;
-        a.xi[i] = (float)(hn + a.bottom[i]);
+        a.xi[i] = (float)hn;
     }
     const int e = a.e_lo + t;
     if (e < a.e_if12_hi) {

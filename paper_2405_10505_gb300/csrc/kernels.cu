@@ -149,11 +149,22 @@ __global__ void fp32_depths(DevMesh m, float *He32, float4 *estat, float4 *vkh) 
     }
 }
 
-__global__ void fp32_shadows(const double *h, const double *b, const double *u, float *xi, float *u32, int nC,
-                             int nE) {
+__global__ void fp32_shadows(const double *xi_state, const double *u, float *xi, float *u32, int nC, int nE) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < nC) xi[t] = (float)(h[t] + b[t]);
+    if (t < nC) xi[t] = (float)xi_state[t];
     if (t < nE) u32[t] = (float)u[t];
+}
+
+// FP64 path: resting thickness H_e per edge (mean of the two cells; a no-flow
+// edge's absent cell is its present one) and H_v per vertex (kite-weighted)
+__global__ void fp64_depths(DevMesh m, double *He64, double *Hv64) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m.nE) He64[t] = -0.5 * (m.bottom[m.coe0[t]] + m.bottom[m.coe1[t]]);
+    if (t < m.nV) {
+        double s = 0.0;
+        for (int j = 0; j < 3; ++j) s += m.cKite[j * m.nV + t] * (-m.bottom[m.cov[j * m.nV + t]]);
+        Hv64[t] = s;
+    }
 }
 
 __global__ void step_end(long long *step) {
@@ -161,9 +172,13 @@ __global__ void step_end(long long *step) {
     *step += 1;
 }
 
-__global__ void gather_kernel(double *dst, const double *src, const int *idx, int n) {
+__global__ void gather_kernel(double *dst, const double *src, const int *idx, int n, const double *b, int sign) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[idx[i]];
+    if (i >= n) return;
+    const int k = idx[i];
+    double v = src[k];
+    if (b) v = sign > 0 ? v + b[i] : v - b[k];
+    dst[i] = v;
 }
 
 __global__ void zero_bnd_kernel(double *u, const unsigned char *ebnd, int n) {
@@ -183,13 +198,13 @@ __device__ double block_sum(double v, double *sh) {
 
 // Fixed-order partial sums (deterministic): thread t of the grid sums
 // elements t, t + G, t + 2G, ...; each block reduces with a fixed tree.
-__global__ void __launch_bounds__(TPB) diag_partials(DevMesh m, const double *h, const double *u,
+__global__ void __launch_bounds__(TPB) diag_partials(DevMesh m, const double *xi, const double *u,
                                                       double *partials) {
     __shared__ double sh[TPB];
     const int G = gridDim.x * blockDim.x;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     double mass = 0.0, vort = 0.0;
-    for (int i = t; i < m.nC; i += G) mass += m.area[i] * h[i];
+    for (int i = t; i < m.nC; i += G) mass += m.area[i] * (xi[i] - m.bottom[i]);
     const int nV = m.nV;
     for (int v = t; v < nV; v += G) {
         double c = 0.0;
@@ -222,10 +237,10 @@ __global__ void __launch_bounds__(TPB) diag_final(const double *partials, int nb
     }
 }
 
-__global__ void check_kernel(const double *h, int nC, const double *u, int nE, int *flag) {
+__global__ void check_kernel(const double *xi, const double *b, int nC, const double *u, int nE, int *flag) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool bad = false;
-    if (i < nC) bad |= !(h[i] > 0.0) || !isfinite(h[i]);
+    if (i < nC) bad |= !(xi[i] - b[i] > 0.0) || !isfinite(xi[i]);
     if (i < nE) bad |= !isfinite(u[i]);
     if (bad) atomicOr(flag, 1);
 }
@@ -331,8 +346,13 @@ cudaError_t launch_fp32_depths(const DevMesh &m, float *He32, float4 *estat,
 }
 
 cudaError_t launch_fp32_shadows(const DevMesh &m, const DevArrays &arr, cudaStream_t st) {
-    fp32_shadows<<<nblk(m.nE > m.nC ? m.nE : m.nC), TPB, 0, st>>>(arr.a[A_H], m.bottom, arr.a[A_U], arr.xi32,
-                                                                   arr.u32, m.nC, m.nE);
+    fp32_shadows<<<nblk(m.nE > m.nC ? m.nE : m.nC), TPB, 0, st>>>(arr.a[A_H], arr.a[A_U], arr.xi32, arr.u32,
+                                                                   m.nC, m.nE);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_depths(const DevMesh &m, double *He64, double *Hv64, cudaStream_t st) {
+    fp64_depths<<<nblk(m.nE > m.nV ? m.nE : m.nV), TPB, 0, st>>>(m, He64, Hv64);
     return cudaGetLastError();
 }
 
@@ -376,9 +396,10 @@ cudaError_t launch_op(const Op &op, const DevMesh &m, const DevArrays &arr, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(double *dst, const double *src, const int *idx, int n, cudaStream_t st) {
+cudaError_t launch_gather(double *dst, const double *src, const int *idx, int n, cudaStream_t st, const double *b,
+                          int sign) {
     if (n <= 0) return cudaSuccess;
-    gather_kernel<<<nblk(n), TPB, 0, st>>>(dst, src, idx, n);
+    gather_kernel<<<nblk(n), TPB, 0, st>>>(dst, src, idx, n, b, sign);
     return cudaGetLastError();
 }
 
@@ -387,15 +408,16 @@ cudaError_t launch_zero_boundary(double *u, const unsigned char *ebnd, int nE, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_diagnostics(const DevMesh &m, const double *h, const double *u, double *partials, int nblocks,
+cudaError_t launch_diagnostics(const DevMesh &m, const double *xi, const double *u, double *partials, int nblocks,
                                double *out2, cudaStream_t st) {
-    diag_partials<<<nblocks, TPB, 0, st>>>(m, h, u, partials);
+    diag_partials<<<nblocks, TPB, 0, st>>>(m, xi, u, partials);
     diag_final<<<1, TPB, 0, st>>>(partials, nblocks, out2);
     return cudaGetLastError();
 }
 
-cudaError_t launch_check(const double *h, int nC, const double *u, int nE, int *flag, cudaStream_t st) {
-    check_kernel<<<nblk(nE > nC ? nE : nC), TPB, 0, st>>>(h, nC, u, nE, flag);
+cudaError_t launch_check(const double *xi, const double *b, int nC, const double *u, int nE, int *flag,
+                         cudaStream_t st) {
+    check_kernel<<<nblk(nE > nC ? nE : nC), TPB, 0, st>>>(xi, b, nC, u, nE, flag);
     return cudaGetLastError();
 }
 

@@ -43,6 +43,10 @@ struct DevMesh {
     const int *rowN, *rowV;             // [nC * rowS] neighbour cell / counter-clockwise vertex per slot
     // resting depth H = -b as seen by the FP32 path: per cell, edge mean, vertex mean (per state)
     const float *He32;
+    // FP64 path (per state): H_e = -(b_c0 + b_c1) / 2 per edge and
+    // H_v = sum_j kite_j H_j / A_v per vertex, the resting thickness that the
+    // flux and the vertex thickness add to the surface elevation xi
+    const double *He64, *Hv64;
 };
 
 struct DevForcing {
@@ -59,7 +63,10 @@ struct DevForcing {
     const long long *step;     // device step counter
 };
 
-// State arrays by schedule id.  FP64 path: every array is double (a[]).
+// State arrays by schedule id.  Every thickness array, the double time level
+// A_H included, holds the surface elevation xi = h + b = h - H (the
+// deviation from the resting depth), so the state rounds at the precision of
+// the displacement, not of the depth.  FP64 path: every array is double (a[]).
 // FP32-tendency path: the time level A_H / A_U, the correction sums A_ACCH /
 // A_ACCU and the saved time level A_SH0 / A_SU0 stay double (a[]); the stage
 // arrays, K, q, F, q_e and the saved IF-1 stage data are float (f[]), with
@@ -87,15 +94,22 @@ cudaError_t launch_fp32_depths(const DevMesh &m, float *He32, float4 *estat,
                                float4 *vkh, cudaStream_t st);
 cudaError_t launch_fp32_shadows(const DevMesh &m, const DevArrays &arr, cudaStream_t st);
 
-// caller-order <-> band-order copies
-cudaError_t launch_gather(double *dst, const double *src, const int *idx, int n, cudaStream_t st);
+// caller-order <-> band-order copies: dst[i] = src[idx[i]] + sign * b[k],
+// k = i (sign +1: h in caller order to xi in band order) or idx[i] (sign -1:
+// xi to h in caller order); b = NULL copies only
+cudaError_t launch_gather(double *dst, const double *src, const int *idx, int n, cudaStream_t st,
+                          const double *b = nullptr, int sign = 0);
+// FP64 path: the resting thickness per edge and vertex (He64, Hv64) from the bottom
+cudaError_t launch_fp64_depths(const DevMesh &m, double *He64, double *Hv64, cudaStream_t st);
 cudaError_t launch_zero_boundary(double *u, const unsigned char *ebnd, int nE, cudaStream_t st);
 
-// deterministic reductions: mass = sum A_i h_i, absolute vorticity = sum_v A_v (zeta_v + f_v)
-cudaError_t launch_diagnostics(const DevMesh &m, const double *h, const double *u, double *partials,
+// deterministic reductions: mass = sum A_i h_i (h = xi - b), absolute
+// vorticity = sum_v A_v (zeta_v + f_v)
+cudaError_t launch_diagnostics(const DevMesh &m, const double *xi, const double *u, double *partials,
                                int nblocks, double *out2, cudaStream_t st);
 constexpr int DIAG_BLOCKS = 608;   // 4 blocks per SM of a 152-SM GB300
-// non-finite or non-positive thickness check; sets *flag to 1
-cudaError_t launch_check(const double *h, int nC, const double *u, int nE, int *flag, cudaStream_t st);
+// non-finite state or non-positive thickness h = xi - b check; sets *flag to 1
+cudaError_t launch_check(const double *xi, const double *b, int nC, const double *u, int nE, int *flag,
+                         cudaStream_t st);
 
 }  // namespace fblts

@@ -395,138 +395,161 @@ private:
 
 }  // namespace
 
-// Algorithmic bytes of one launch: every array element that its arithmetic
-// reads or writes, once, at storage size (int32 4, double 8, float 4, flag 1,
-// 16-byte records 16), with gathered arrays counted over the distinct
-// elements the launch touches (exact, from the mesh incidence).  A padded
-// row counts at its stored width.  FP32: stage data, kinetic energy, PV,
-// edge records and coefficients in float; the time level, 1/A and the
-// correction sums in double.
-void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
-    Toucher tch(hm);
+// Bytes of one launch under two models, each counting every array element once
+// per launch at its storage size (int32 4, double 8, float 4, flag 1), with
+// gathered arrays counted over the distinct elements the launch touches
+// (exact, from the mesh incidence):
+//   algorithmic - the arrays the stage's arithmetic needs (Eq. trisk_thickness,
+//     Eq. trisk_vorticity, Eq. fbrk32): state, stage values and the
+//     intermediates K, q, h*, F, the mesh metadata at its real length (no row
+//     padding, no record padding) and with the metric factors per edge and per
+//     cell (d_e, l_e, 1/A_i) rather than folded into per-slot copies.  The
+//     per-slot shares of the cell-side TRiSK form are an intermediate of this
+//     implementation only and count nothing: the math of Phi is counted where
+//     its inputs are read.
+//   moved - what the kernels of this library read and write: padded rows at
+//     their stored width, 16-byte records, per-slot coefficients and the
+//     shares (written by the TRiSK pass, read by the edge pass).
+// FP32: stage data, kinetic energy, PV and coefficients in float; the time
+// level, 1/A and the correction sums in double.
+static double op_bytes(const HostMesh &hm, Toucher &tch, const Op &op, int forcing, bool fp32, bool alg) {
     const double R = fp32 ? 4.0 : 8.0;        // stage / scratch element
     const double C = fp32 ? 4.0 : 8.0;        // coefficient element
+    const double REC = alg ? 12.0 : 16.0;     // {3 floats} record, padded to 16 bytes in memory
     const bool vortex = (forcing & FBLTS_FORCE_VORTEX) != 0;
-    for (Op &op : s.ops) {
-        double b = 0.0;
-        std::vector<std::pair<int, int>> all;
-        for (int k = 0; k < op.nseg; ++k)
-            if (op.seg[k].end > op.seg[k].begin) all.emplace_back(op.seg[k].begin, op.seg[k].end);
-        auto per_mode = [&](double n, int mode, bool cell) {
-            double x = 0.0;
-            if (mode == SEG_UPD)   // stage inputs at the element, stage output (+ FB average for cells)
-                x = cell ? n * R * (3 + (op.stage == 3 ? 1 : 0)) : n * 2 * R;
-            if (mode == SEG_INPLACE) {
-                if (cell) x = fp32 ? n * (16 + 8 + 4 + 4 + 4 + (op.stage == 3 ? 4 : 0)) : n * (16 + 8 + 8);
-                else x = fp32 ? n * (16 + 4) : n * 16;
-            }
-            if (mode == SEG_ACC_SET) x = n * 8;
-            if (mode == SEG_ACC_ADD) x = n * 16;
-            if (mode == SEG_PHI) x = n * R;
-            // RK4: as SEG_UPD (the previous stage is the element's own input) plus
-            // the tendency sum (write, or read and write); the final stage as
-            // SEG_INPLACE plus the sum read
-            if (mode == SEG_RK_SET || mode == SEG_RK_ADD2) x = n * ((cell ? 3 : 2) * R + (mode == SEG_RK_SET ? 8 : 16));
-            if (mode == SEG_RK_FIN) {
-                if (cell) x = fp32 ? n * (16 + 8 + 4 + 4 + 4 + 8) : n * (16 + 8 + 8);
-                else x = fp32 ? n * (16 + 4 + 8) : n * (16 + 8);
-            }
-            return x;
-        };
-        switch (op.kind) {
-            case OP_CELL: {
-                if (all.empty()) break;
-                // cells: nEoC, 1/A, K out; rows (signed edge, neighbour cell);
-                // edges: u_in and (fp32) the 16-byte record {l, d l / 4, H_e}
-                // or (fp64) the per-slot coefficients; xi / h at the cells
-                bool konly = true;
-                for (int k = 0; k < op.nseg; ++k) konly = konly && op.seg[k].mode == SEG_KONLY;
-                const Touched &t = tch.get(OP_CELL, all);
-                b += t.self * (4 + (fp32 ? 8 : 0) + R) + t.slots * 4 + t.edges * (R + (fp32 ? 16 : 0));
-                if (!fp32) b += t.slots * C;                           // cKE
-                if (!konly) b += t.slots * (4 + (fp32 ? 0 : C)) + t.cells * R;   // coc (+ cDiv), h_in
-                for (int k = 0; k < op.nseg; ++k)
-                    b += per_mode(op.seg[k].end - op.seg[k].begin, op.seg[k].mode, true);
-            } break;
-            case OP_VERT: {
-                const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
-                const Touched &t = tch.get(OP_VERT, r);
-                // eov, cov, cVort, cKite, f, (fp32) H_v, q out | u_in, hst
-                b = t.self * (3 * (4 + 4 + C + C) + C + (fp32 ? 4 : 0) + R) + t.edges * R + t.cells * R;
-            } break;
-            case OP_EPREP: {
-                const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
-                const Touched &t = tch.get(OP_EPREP, r);
-                // coe, voe, u_in, (fp32) l_e, H_e and the 16-byte record out,
-                // (fp64) ebnd and F, q_e, F q_e out | hst at cells, q at vertices
-                b = t.self * (16 + R + (fp32 ? 4 + 4 + 16 : 1 + 3 * R)) + t.cells * R + t.verts * R;
-            } break;
-            case OP_TRISK: {
-                const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
-                const Touched &t = tch.get(OP_TRISK, r);
-                // cells: nEoC, K, rows {signed edge, kite prefix, neighbour cell,
-                // vertex} at their stored width, (vortex) p_s, one 16-byte share
-                // out per slot | edges: u_in, {l, d l / 4, H_e} | hst at the cells
-                // and their neighbours | q at the vertices
-                b = t.self * (4 + R + hm.rowS * 16 + (vortex ? R : 0)) + t.slots * 16 + t.edges * (R + 16) +
-                    t.cells * R + t.verts * R;
-            } break;
-            case OP_EDGE: {
-                if (all.empty()) break;
-                if (op.split == 2) {
-                    // splitting stage: ebnd, coe, 1/d_e, the slow part | the FB-averaged
-                    // thickness at the cells (+ bottom in double)
-                    const Touched &t = tch.get(OP_EPREP, all);
-                    b += t.self * (1 + 8 + C + R) + t.cells * (R + (fp32 ? 0 : 8));
-                    for (int k = 0; k < op.nseg; ++k)
-                        b += per_mode(op.seg[k].end - op.seg[k].begin, op.seg[k].mode, false);
-                    break;
-                }
-                if (fp32 && hm.rows_canonical) {
-                    // ebnd, 1/d_e, the two cells' 16-byte shares
-                    for (int k = 0; k < op.nseg; ++k) {
-                        const double n = op.seg[k].end - op.seg[k].begin;
-                        b += n * (1 + 4 + 32) + per_mode(n, op.seg[k].mode, false);
-                        if (forcing) b += n * (R + 4 + 3 * R);   // u_in, H_e, wind, C_W
-                    }
-                    break;
-                }
-                const Touched &t = tch.get(OP_EDGE, all);
-                // explicit neighbour lists: ebnd, coe, invDc | K, hst at cells (+ bottom
-                // in double) | neighbour records | nEoE, eoe, woe
-                b += t.self * (1 + 8 + C) + t.cells * (2 * R + (fp32 ? 0 : 8));
-                if (fp32) b += t.edges * 16;                  // {l F, q_e, l u} (own q_e included)
-                else b += t.edges * 2 * R + t.self * R;       // F, F q_e at the neighbours, own q_e
-                b += t.self * 4 + t.slots * (4 + C);
-                if (forcing) {
-                    // u_in (fp64: at the neighbours too), H_e (fp32), wind, C_W; surface pressure at cells
-                    b += fp32 ? t.self * (R + 4 + 3 * R) : t.self * 3 * R + t.edges * R;
-                    if (vortex) b += t.cells * R;
-                }
+    double b = 0.0;
+    std::vector<std::pair<int, int>> all;
+    for (int k = 0; k < op.nseg; ++k)
+        if (op.seg[k].end > op.seg[k].begin) all.emplace_back(op.seg[k].begin, op.seg[k].end);
+    auto per_mode = [&](double n, int mode, bool cell) {
+        double x = 0.0;
+        if (mode == SEG_UPD)   // stage inputs at the element, stage output (+ FB average for cells)
+            x = cell ? n * R * (3 + (op.stage == 3 ? 1 : 0)) : n * 2 * R;
+        if (mode == SEG_INPLACE) {
+            if (cell) x = fp32 ? n * (16 + 8 + 4 + 4 + 4 + (op.stage == 3 ? 4 : 0)) : n * (16 + 8 + 8);
+            else x = fp32 ? n * (16 + 4) : n * 16;
+        }
+        if (mode == SEG_ACC_SET) x = n * 8;
+        if (mode == SEG_ACC_ADD) x = n * 16;
+        if (mode == SEG_PHI) x = n * R;
+        // RK4: as SEG_UPD (the previous stage is the element's own input) plus
+        // the tendency sum (write, or read and write); the final stage as
+        // SEG_INPLACE plus the sum read
+        if (mode == SEG_RK_SET || mode == SEG_RK_ADD2) x = n * ((cell ? 3 : 2) * R + (mode == SEG_RK_SET ? 8 : 16));
+        if (mode == SEG_RK_FIN) {
+            if (cell) x = fp32 ? n * (16 + 8 + 4 + 4 + 4 + 8) : n * (16 + 8 + 8);
+            else x = fp32 ? n * (16 + 4 + 8) : n * (16 + 8);
+        }
+        return x;
+    };
+    switch (op.kind) {
+        case OP_CELL: {
+            if (all.empty()) break;
+            // cells: nEoC, K out, (alg, or fp32) 1/A; rows (signed edge,
+            // neighbour cell); edges: u_in and the metrics l_e, d_e l_e / 4
+            // (fp32: one record with H_e; fp64 moved: per-slot coefficients
+            // with 1/A folded in); xi / h at the cells
+            bool konly = true;
+            for (int k = 0; k < op.nseg; ++k) konly = konly && op.seg[k].mode == SEG_KONLY;
+            const Touched &t = tch.get(OP_CELL, all);
+            b += t.self * (4 + R) + t.slots * 4 + t.edges * R;
+            if (fp32) b += t.self * 8 + t.edges * REC;
+            else if (alg) b += t.self * 8 + t.edges * 2 * C;
+            else b += t.slots * C;                                  // cKE per slot
+            if (!konly) b += t.slots * (4 + (fp32 || alg ? 0 : C)) + t.cells * R;   // coc (+ cDiv), h_in
+            if (!konly && !fp32) b += t.edges * 8;                  // H_e
+            for (int k = 0; k < op.nseg; ++k)
+                b += per_mode(op.seg[k].end - op.seg[k].begin, op.seg[k].mode, true);
+        } break;
+        case OP_VERT: {
+            const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
+            const Touched &t = tch.get(OP_VERT, r);
+            // eov, cov, t d / A_v, kite / A_v, f, H_v, q out | u_in, hst
+            b = t.self * (3 * (4 + 4 + C + C) + C + C + R) + t.edges * R + t.cells * R;
+        } break;
+        case OP_EPREP: {
+            const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
+            const Touched &t = tch.get(OP_EPREP, r);
+            // coe, voe, u_in, (fp32) l_e, H_e and the record {l F, q_e, l u} out,
+            // (fp64) ebnd, H_e and F, q_e, F q_e out | hst at cells, q at vertices
+            b = t.self * (16 + R + (fp32 ? 4 + 4 + REC : 1 + 8 + 3 * R)) + t.cells * R + t.verts * R;
+        } break;
+        case OP_TRISK: {
+            const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
+            const Touched &t = tch.get(OP_TRISK, r);
+            // cells: nEoC, K, rows {signed edge, kite prefix, neighbour cell,
+            // vertex} (moved: at their stored width, and one 16-byte share out
+            // per slot), (vortex) p_s | edges: u_in, l_e and H_e (moved: the
+            // record {l, d l / 4, H_e}) | hst at the cells and their neighbours
+            // | q at the vertices
+            const double rows = alg ? t.slots * 16 : t.self * hm.rowS * 16;
+            b = t.self * (4 + R + (vortex ? R : 0)) + rows + t.edges * (R + (alg ? 2 * C : 16)) + t.cells * R +
+                t.verts * R;
+            if (!alg) b += t.slots * 16;
+        } break;
+        case OP_EDGE: {
+            if (all.empty()) break;
+            if (op.split == 2) {
+                // splitting stage: ebnd, coe, 1/d_e, the slow part | the FB-averaged
+                // surface elevation at the cells
+                const Touched &t = tch.get(OP_EPREP, all);
+                b += t.self * (1 + 8 + C + R) + t.cells * R;
                 for (int k = 0; k < op.nseg; ++k)
                     b += per_mode(op.seg[k].end - op.seg[k].begin, op.seg[k].mode, false);
-            } break;
-            case OP_SAVE: {
-                const double big = fp32 ? (16 + 3 * 8) : 64;   // h^n copy + 3 stage copies
-                b = big * (op.c_if1_hi - op.c_if1_lo) + 16.0 * (op.c_if12_hi - op.c_if1_hi) +
-                    big * (op.e_if1_hi - op.e_if1_lo) + 16.0 * (op.e_if12_hi - op.e_if1_hi);
-            } break;
-            case OP_PRED:
-                b = (fp32 ? 52.0 : 80.0) * (op.c_if1_hi - op.c_if1_lo) +
-                    (fp32 ? 32.0 : 56.0) * (op.e_if1_hi - op.e_if1_lo);
                 break;
-            case OP_FINAL:
-                b = (fp32 ? 36.0 : 24.0) * (op.c_if12_hi - op.c_if1_lo) +
-                    (fp32 ? 29.0 : 25.0) * (op.e_if12_hi - op.e_if1_lo);
+            }
+            if (fp32 && hm.rows_canonical) {
+                // ebnd, 1/d_e (moved: the two cells' 16-byte shares)
+                for (int k = 0; k < op.nseg; ++k) {
+                    const double n = op.seg[k].end - op.seg[k].begin;
+                    b += n * (1 + 4 + (alg ? 0 : 32)) + per_mode(n, op.seg[k].mode, false);
+                    if (forcing) b += n * (R + 4 + 3 * R);   // u_in, H_e, wind, C_W
+                }
                 break;
-            case OP_FORCING:
-                if (forcing)
-                    b = (double)hm.nE * (16 + 3 * R + (vortex ? 16 : 0)) + (double)hm.nC * (R + (vortex ? 16 : 0));
-                break;
-            case OP_STEP_END: b = 16; break;
-            default: break;
-        }
-        op.alg_bytes = b;
+            }
+            const Touched &t = tch.get(OP_EDGE, all);
+            // explicit neighbour lists: ebnd, coe, invDc | K, hst at cells |
+            // neighbour records | nEoE, eoe, woe
+            b += t.self * (1 + 8 + C) + t.cells * 2 * R;
+            if (fp32) b += t.edges * REC;                 // {l F, q_e, l u} (own q_e included)
+            else b += t.edges * 2 * R + t.self * R;       // F, F q_e at the neighbours, own q_e
+            b += t.self * 4 + t.slots * (4 + C);
+            if (forcing) {
+                // u_in (fp64: at the neighbours too), H_e, wind, C_W; surface pressure at cells
+                b += fp32 ? t.self * (R + 4 + 3 * R) : t.self * (3 * R + 8) + t.edges * R;
+                if (vortex) b += t.cells * R;
+            }
+            for (int k = 0; k < op.nseg; ++k)
+                b += per_mode(op.seg[k].end - op.seg[k].begin, op.seg[k].mode, false);
+        } break;
+        case OP_SAVE: {
+            const double big = fp32 ? (16 + 3 * 8) : 64;   // h^n copy + 3 stage copies
+            b = big * (op.c_if1_hi - op.c_if1_lo) + 16.0 * (op.c_if12_hi - op.c_if1_hi) +
+                big * (op.e_if1_hi - op.e_if1_lo) + 16.0 * (op.e_if12_hi - op.e_if1_hi);
+        } break;
+        case OP_PRED:
+            b = (fp32 ? 52.0 : 80.0) * (op.c_if1_hi - op.c_if1_lo) +
+                (fp32 ? 32.0 : 56.0) * (op.e_if1_hi - op.e_if1_lo);
+            break;
+        case OP_FINAL:
+            b = (fp32 ? 36.0 : 24.0) * (op.c_if12_hi - op.c_if1_lo) +
+                (fp32 ? 29.0 : 25.0) * (op.e_if12_hi - op.e_if1_lo);
+            break;
+        case OP_FORCING:
+            if (forcing)
+                b = (double)hm.nE * (16 + 3 * R + (vortex ? 16 : 0)) + (double)hm.nC * (R + (vortex ? 16 : 0));
+            break;
+        case OP_STEP_END: b = 16; break;
+        default: break;
+    }
+    return b;
+}
+
+void schedule_bytes(const HostMesh &hm, int forcing, bool fp32, Schedule &s) {
+    Toucher tch(hm);
+    for (Op &op : s.ops) {
+        op.alg_bytes = op_bytes(hm, tch, op, forcing, fp32, true);
+        op.moved_bytes = op_bytes(hm, tch, op, forcing, fp32, false);
     }
 }
 
