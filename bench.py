@@ -499,6 +499,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000, help="timed coarse steps (latency percentiles over them)")
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--latency-steps", type=int, default=1000,
+                    help="coarse steps of the latency window (p50/p99), at least --steps")
     ap.add_argument("--impl", default="fblts", choices=["fblts", "reference"])
     ap.add_argument("--workload", default="basin")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
@@ -583,7 +585,7 @@ def main():
 
     # latency percentiles over a window of at least 1000 coarse steps (after the
     # timed region, whatever --steps is), one event pair per step
-    n_lat = max(1000, args.steps)
+    n_lat = max(args.latency_steps, args.steps)
     if n_lat > args.steps:
         levs = [torch.cuda.Event(enable_timing=True) for _ in range(n_lat + 1)]
         levs[0].record(stream)

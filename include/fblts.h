@@ -102,12 +102,19 @@ const char *fblts_last_error(void);
  *  nIF1Layers, nIF2Layers cell layers of the IF-1 / IF-2 bands (0 = 2, the
  *                         stencil radius of TRiSK, Sec. 2.2).
  *
+ *  flags                  FBLTS_MESH_* bits (0 = none).
+ *
  * Layout rules checked by fblts_mesh_create (FBLTS_E_REGIONS otherwise):
  * level l cells adjacent only to levels l-1, l, l+1, and for three or more
  * levels every level l-1 cell at least 10 + nIF1 + nIF2 + 3 cell layers (17
  * with the default bands) from every level >= l+1 cell, so that the F^5 band
- * of one level pair and the interface bands of the next stay disjoint.
+ * of one level pair and the interface bands of the next stay disjoint.  With
+ * FBLTS_MESH_PROMOTE_LEVELS the library enforces the separation itself: a
+ * level l-1 cell closer than that to a level >= l+1 cell is moved to level l
+ * (a smaller time step, so stability is kept), repeated until nothing
+ * changes; fblts_mesh_levels returns the levels in use.
  */
+enum { FBLTS_MESH_PROMOTE_LEVELS = 1 };
 typedef struct fblts_mesh_desc {
     int32_t nCells, nEdges, nVertices, maxEdges, maxEdges2;
     const int32_t *cellsOnEdge;
@@ -131,6 +138,7 @@ typedef struct fblts_mesh_desc {
     int32_t nLevels;
     const int32_t *M;
     int32_t nIF1Layers, nIF2Layers;
+    int32_t flags;
 } fblts_mesh_desc;
 
 /* Validates, classifies the LTS regions (Sec. 2.2: F, F^1..F^5, IF-1, IF-2,
@@ -143,6 +151,11 @@ fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mesh **out);
  * taken and its server not destroyed: all of them read the mesh's device
  * tables. */
 fblts_status fblts_mesh_destroy(fblts_mesh *mesh);
+
+/* The LTS level of every cell (caller order) as the mesh uses it: ltsLevel,
+ * or after the promotion of FBLTS_MESH_PROMOTE_LEVELS.  level_out[nCells]
+ * is caller-owned.  Host only. */
+fblts_status fblts_mesh_levels(const fblts_mesh *mesh, int32_t *level_out);
 
 /* Counts derived by fblts_mesh_create (host only, no device work). */
 typedef struct fblts_mesh_info {
@@ -290,8 +303,10 @@ fblts_status fblts_diagnostics(const fblts_state *state, double *total_mass,
 /* Coarse steps done and the current time. */
 fblts_status fblts_state_time(const fblts_state *state, int64_t *steps, double *time);
 
-/* Checkpoint: serialises (step, time, h, u) to buf.  With buf == NULL only
- * *len is set to the size needed.  Synchronises. */
+/* Checkpoint: serialises (step, time, xi, u) to buf, with xi = h + b the
+ * surface elevation the state stores (caller order), so that a run resumed
+ * from it is bitwise the uninterrupted run.  With buf == NULL only *len is
+ * set to the size needed.  Synchronises. */
 fblts_status fblts_state_save(const fblts_state *state, void *buf, size_t *len);
 /* Restores a checkpoint written by fblts_state_save for the same mesh. */
 fblts_status fblts_state_load(fblts_state *state, const void *buf, size_t len);

@@ -25,6 +25,7 @@ REGION_FINE, REGION_IF1, REGION_IF2, REGION_INTERIOR, REGION_OUTSIDE = range(5)
  SEG_RK4_ADD2, SEG_RK4_FINAL) = range(10)
 SCHEME_FBLTS, SCHEME_RK4 = 0, 1
 FORCE_WIND_STRESS, FORCE_BOTTOM_DRAG, FORCE_VORTEX = 1, 2, 4
+MESH_PROMOTE_LEVELS = 1
 PAPER_BETA = (0.531, 0.531, 0.313)   # Sec. 2.1, CFL-optimised FB weights
 
 _PI = C.POINTER(C.c_int32)
@@ -40,7 +41,7 @@ class MeshDesc(C.Structure):
                 ("dcEdge", _PD), ("dvEdge", _PD), ("areaCell", _PD), ("kiteAreasOnVertex", _PD),
                 ("fVertex", _PD), ("angleEdge", _PD), ("xCell", _PD), ("yCell", _PD),
                 ("xEdge", _PD), ("yEdge", _PD), ("ltsLevel", _PI), ("nLevels", C.c_int32),
-                ("M", _PI), ("nIF1Layers", C.c_int32), ("nIF2Layers", C.c_int32)]
+                ("M", _PI), ("nIF1Layers", C.c_int32), ("nIF2Layers", C.c_int32), ("flags", C.c_int32)]
 
 
 class MeshInfo(C.Structure):
@@ -102,6 +103,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_TAKEN = range(5)
 
 _LIB = None
 SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts_mesh_get_info", "fblts_mesh_regions",
+           "fblts_mesh_levels",
            "fblts_plan_step", "fblts_plan_op",
            "fblts_state_init", "fblts_state_destroy", "fblts_lts_advance", "fblts_synchronize",
            "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
@@ -133,6 +135,7 @@ def lib():
             "fblts_mesh_create": [C.POINTER(MeshDesc), C.POINTER(V)],
             "fblts_mesh_destroy": [V],
             "fblts_mesh_get_info": [V, C.POINTER(MeshInfo)],
+            "fblts_mesh_levels": [V, _PI],
             "fblts_mesh_regions": [C.POINTER(MeshDesc), C.c_int32, _PI, _PI, _PI, _PI],
             "fblts_plan_step": [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(C.c_int64), _PD,
                                 C.POINTER(C.c_int64)],
@@ -236,18 +239,20 @@ class State:
             pass
 
 
-def mesh_create(m, fVertex, level=None, M=None, nIF1=0, nIF2=0):
-    """fblts_mesh_create from MPAS-named arrays on ``m`` (any object with those attributes)."""
-    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2)
+def mesh_create(m, fVertex, level=None, M=None, nIF1=0, nIF2=0, promote=False):
+    """fblts_mesh_create from MPAS-named arrays on ``m`` (any object with those
+    attributes); ``promote`` sets FBLTS_MESH_PROMOTE_LEVELS (the library then
+    separates the levels itself; ``mesh_levels`` returns the levels in use)."""
+    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2, promote)
     h = C.c_void_p()
     _check(lib().fblts_mesh_create(C.byref(d), C.byref(h)))
     return Mesh(h, keep)
 
 
-def mesh_regions(m, fVertex, level, M, pair, nIF1=0, nIF2=0):
+def mesh_regions(m, fVertex, level, M, pair, nIF1=0, nIF2=0, promote=False):
     """fblts_mesh_regions (host only): per cell and per edge, caller order, the
     region class of the level pair (pair, pair + 1) and the F^b band."""
-    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2)
+    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2, promote)
     cc = np.empty(int(m.nCells), np.int32)
     cb = np.empty(int(m.nCells), np.int32)
     ec = np.empty(int(m.nEdges), np.int32)
@@ -256,10 +261,10 @@ def mesh_regions(m, fVertex, level, M, pair, nIF1=0, nIF2=0):
     return cc, cb, ec, eb
 
 
-def plan_step(m, fVertex, level, M, params, nIF1=0, nIF2=0):
+def plan_step(m, fVertex, level, M, params, nIF1=0, nIF2=0, promote=False):
     """fblts_plan_step (host only): (launches, algorithmic bytes, cell-updates)
     of one coarse step for these parameters."""
-    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2)
+    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2, promote)
     n, cu = C.c_int64(), C.c_int64()
     b = C.c_double()
     _check(lib().fblts_plan_step(C.byref(d), C.byref(params), C.byref(n), C.byref(b), C.byref(cu)))
@@ -281,7 +286,7 @@ def plan_op(m, fVertex, level, M, params, index, nIF1=0, nIF2=0):
     return name, int(st.value), (buf[: int(n)].copy() if n is not None else None)
 
 
-def _mesh_desc(m, fVertex, level, M, nIF1, nIF2):
+def _mesh_desc(m, fVertex, level, M, nIF1, nIF2, promote=False):
     keep = {}
 
     def I(name, arr=None):
@@ -316,7 +321,8 @@ def _mesh_desc(m, fVertex, level, M, nIF1, nIF2):
                  I("nEdgesOnEdge"), I("edgesOnEdge"), D("weightsOnEdge"), D("dcEdge"), D("dvEdge"),
                  D("areaCell"), D("kiteAreasOnVertex"), D("fVertex", fVertex),
                  D("angleEdge", optional=True), D("xCell", optional=True), D("yCell", optional=True),
-                 D("xEdge", optional=True), D("yEdge", optional=True), lev_p, nL, M_p, int(nIF1), int(nIF2))
+                 D("xEdge", optional=True), D("yEdge", optional=True), lev_p, nL, M_p, int(nIF1), int(nIF2),
+                 MESH_PROMOTE_LEVELS if promote else 0)
     keep["desc"] = d
     return d, keep
 
@@ -328,6 +334,14 @@ def mesh_destroy(mesh):
     if h:
         _check(lib().fblts_mesh_destroy(h))
         mesh.handle = None
+
+
+def mesh_levels(mesh):
+    """fblts_mesh_levels: the LTS level of every cell (caller order) in use."""
+    info = mesh_get_info(mesh)
+    out = np.empty(int(info.nCells), np.int32)
+    _check(lib().fblts_mesh_levels(mesh.handle, _p(out, _PI)))
+    return out
 
 
 def mesh_get_info(mesh):

@@ -315,6 +315,13 @@ extern "C" fblts_status fblts_plan_step(const fblts_mesh_desc *desc, const fblts
     return FBLTS_OK;
 }
 
+extern "C" fblts_status fblts_mesh_levels(const fblts_mesh *m, int32_t *level_out) {
+    if (!m || !level_out) { set_error("mesh_levels: NULL argument"); return FBLTS_E_ARG; }
+    const HostMesh &hm = m->hm;
+    for (int i = 0; i < hm.nC; ++i) level_out[hm.cell_n2o[i]] = hm.level[i];
+    return FBLTS_OK;
+}
+
 extern "C" fblts_status fblts_mesh_get_info(const fblts_mesh *m, fblts_mesh_info *info) {
     if (!m || !info) { set_error("mesh_get_info: NULL argument"); return FBLTS_E_ARG; }
     std::memset(info, 0, sizeof(*info));
@@ -376,12 +383,14 @@ extern "C" fblts_status fblts_state_destroy(fblts_state *s) {
     return FBLTS_OK;
 }
 
-static fblts_status upload_state(fblts_state *s, const double *h, const double *u) {
+// h holds the thickness, or with raw = true the surface elevation xi = h + b
+// itself (checkpoints: the state's exact bits)
+static fblts_status upload_state(fblts_state *s, const double *h, const double *u, bool raw = false) {
     const fblts_mesh *m = s->mesh;
     const int nC = m->hm.nC, nE = m->hm.nE;
     if (h) {   // the time level holds the surface elevation xi = h + b
         CK(cudaMemcpyAsync(s->d_stage_c, h, sizeof(double) * nC, cudaMemcpyHostToDevice, s->st));
-        CK(launch_gather(s->arr.a[A_H], s->d_stage_c, m->cell_n2o, nC, s->st, s->dm.bottom, +1));
+        CK(launch_gather(s->arr.a[A_H], s->d_stage_c, m->cell_n2o, nC, s->st, raw ? nullptr : s->dm.bottom, +1));
     }
     if (u) {
         CK(cudaMemcpyAsync(s->d_stage_e, u, sizeof(double) * nE, cudaMemcpyHostToDevice, s->st));
@@ -656,12 +665,12 @@ extern "C" fblts_status fblts_synchronize(fblts_state *s) {
     return sync_and_check(s);
 }
 
-extern "C" fblts_status fblts_state_read(const fblts_state *s, double *h_out, double *u_out) {
-    if (!s) { set_error("state_read: NULL state"); return FBLTS_E_ARG; }
+// caller-order copies of h = xi - b (raw: of xi itself) and u; synchronises
+static fblts_status read_state(const fblts_state *s, double *h_out, double *u_out, bool raw) {
     const fblts_mesh *m = s->mesh;
     const int nC = m->hm.nC, nE = m->hm.nE;
-    if (h_out) {   // h = xi - b
-        CK(launch_gather(s->d_stage_c, s->arr.a[A_H], m->cell_o2n, nC, s->st, s->dm.bottom, -1));
+    if (h_out) {
+        CK(launch_gather(s->d_stage_c, s->arr.a[A_H], m->cell_o2n, nC, s->st, raw ? nullptr : s->dm.bottom, -1));
         CK(cudaMemcpyAsync(h_out, s->d_stage_c, sizeof(double) * nC, cudaMemcpyDeviceToHost, s->st));
     }
     if (u_out) {
@@ -669,6 +678,11 @@ extern "C" fblts_status fblts_state_read(const fblts_state *s, double *h_out, do
         CK(cudaMemcpyAsync(u_out, s->d_stage_e, sizeof(double) * nE, cudaMemcpyDeviceToHost, s->st));
     }
     return sync_and_check(s);
+}
+
+extern "C" fblts_status fblts_state_read(const fblts_state *s, double *h_out, double *u_out) {
+    if (!s) { set_error("state_read: NULL state"); return FBLTS_E_ARG; }
+    return read_state(s, h_out, u_out, false);
 }
 
 extern "C" fblts_status fblts_state_write(fblts_state *s, const double *h, const double *u) {
@@ -719,11 +733,12 @@ extern "C" fblts_status fblts_state_save(const fblts_state *s, void *buf, size_t
     if (!buf) { *len = need; return FBLTS_OK; }
     if (*len < need) { set_error("state_save: buffer of %zu bytes, need %zu", *len, need); return FBLTS_E_ARG; }
     CkptHeader hd;
-    std::memcpy(hd.magic, "FBLTSCK1", 8);
+    std::memcpy(hd.magic, "FBLTSCK2", 8);
     hd.nC = nC; hd.nE = nE; hd.steps = s->steps; hd.t0 = s->p.t0; hd.dt = s->p.dt;
     std::memcpy(buf, &hd, sizeof(hd));
+    // the surface elevation xi = h + b as stored (the state's exact bits), and u
     double *h = (double *)((char *)buf + sizeof(hd));
-    fblts_status st = fblts_state_read(s, h, h + nC);
+    fblts_status st = read_state(s, h, h + nC, true);
     *len = need;
     return st;
 }
@@ -734,13 +749,13 @@ extern "C" fblts_status fblts_state_load(fblts_state *s, const void *buf, size_t
     CkptHeader hd;
     if (len < sizeof(hd)) { set_error("state_load: buffer too small"); return FBLTS_E_STATE; }
     std::memcpy(&hd, buf, sizeof(hd));
-    if (std::memcmp(hd.magic, "FBLTSCK1", 8) != 0 || hd.nC != nC || hd.nE != nE ||
+    if (std::memcmp(hd.magic, "FBLTSCK2", 8) != 0 || hd.nC != nC || hd.nE != nE ||
         len < sizeof(hd) + sizeof(double) * ((size_t)nC + nE)) {
         set_error("state_load: checkpoint does not match this mesh");
         return FBLTS_E_STATE;
     }
     const double *h = (const double *)((const char *)buf + sizeof(hd));
-    fblts_status st = upload_state(s, h, h + nC);
+    fblts_status st = upload_state(s, h, h + nC, true);
     if (st != FBLTS_OK) return st;
     long long step = hd.steps;
     CK(cudaMemcpyAsync(s->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, s->st));

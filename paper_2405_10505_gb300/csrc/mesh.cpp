@@ -236,6 +236,29 @@ fblts_status build_host_mesh(const fblts_mesh_desc *d, HostMesh &hm) {
         off.swap(off2);
         nbr.swap(nbr2);
     }
+    // optional promotion: level l-1 cells closer than the separation the band
+    // order needs to a level >= l+1 cell move to level l, until stable
+    if ((d->flags & FBLTS_MESH_PROMOTE_LEVELS) && L >= 3) {
+        std::vector<uint8_t> sd(nC);
+        std::vector<int> dd;
+        bool changed = true;
+        for (int it = 0; changed && it < 64; ++it) {
+            changed = false;
+            for (int l = 1; l + 1 < L; ++l) {
+                for (int i = 0; i < nC; ++i) sd[i] = lev[i] >= l + 1;
+                bfs(nC, off, nbr, sd, dd);
+                for (int i = 0; i < nC; ++i)
+                    if (lev[i] <= l - 1 && dd[i] < 10 + hm.kin_cap) {
+                        per_level[lev[i]]--;
+                        per_level[l]++;
+                        lev[i] = l;
+                        changed = true;
+                    }
+            }
+        }
+        for (int l = 0; l < L; ++l)
+            if (per_level[l] == 0) { set_error("mesh_create: level %d has no cells after promotion", l); return FBLTS_E_REGIONS; }
+    }
     for (int e = 0; e < nE; ++e)
         if (!ebnd[e] && std::abs(lev[coe[2 * e]] - lev[coe[2 * e + 1]]) > 1) {
             set_error("mesh_create: edge %d joins levels %d and %d", e, lev[coe[2 * e]], lev[coe[2 * e + 1]]);

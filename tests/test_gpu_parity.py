@@ -233,3 +233,28 @@ def test_mesh_destroy_refused_while_in_use():
     fb.server_destroy(srv)
     fb.mesh_destroy(mesh)
     assert mesh.handle is None
+
+
+def test_promoted_levels_run_and_match_the_oracle():
+    """Nested disks without the separation the band order needs: refused as
+    given, accepted with FBLTS_MESH_PROMOTE_LEVELS; the run then matches the
+    oracle on the levels the library reports (fblts_mesh_levels)."""
+    s = scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3))
+    Lx, Ly = s.mesh.period
+    dx = scenario._min_image(s.mesh.xCell - Lx / 2, Lx)
+    dy = scenario._min_image(s.mesh.yCell - Ly / 2, Ly)
+    r2 = dx ** 2 + dy ** 2
+    raw = np.zeros(s.mesh.nCells, np.int32)
+    raw[r2 <= 190e3 ** 2] = 1
+    raw[r2 <= 50e3 ** 2] = 2
+    with pytest.raises(fb.FbltsError):
+        fb.mesh_create(s.mesh, s.fVertex, level=raw, M=s.M)
+    mesh = fb.mesh_create(s.mesh, s.fVertex, level=raw, M=s.M, promote=True)
+    lev = fb.mesh_levels(mesh)
+    assert (lev >= raw).all() and not np.array_equal(lev, raw)
+    st = make_state(s, mesh=mesh)
+    fb.lts_advance(st, 20)
+    h, u = fb.state_read(st)
+    ho, uo = _oracle(s, 20, level=lev)
+    dh, du = rel_errors(h, u, ho, uo)
+    assert dh <= TOL and du <= TOL, (dh, du)

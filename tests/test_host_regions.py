@@ -47,3 +47,30 @@ def test_regions_reject_a_bad_pair():
     with pytest.raises(fb.FbltsError) as e:
         fb.mesh_regions(s.mesh, s.fVertex, s.level, s.M, 1)
     assert e.value.status == fb.E_ARG
+
+
+def test_library_promotes_levels_like_the_generator():
+    """FBLTS_MESH_PROMOTE_LEVELS: nested disks placed without the separation
+    the band order needs are refused as given and accepted with the flag; the
+    levels the library then uses (read back from the region classes: a cell's
+    level is the number of pairs in whose fine region it lies) are those of
+    the generator's promotion rule (level l-1 cells closer than 17 layers to
+    level >= l+1 move to level l, until stable)."""
+    s = scenario.nested_disk_case(nx=64, ny=64, radii=(190e3, 50e3))
+    Lx, Ly = s.mesh.period
+    dx = scenario._min_image(s.mesh.xCell - Lx / 2, Lx)
+    dy = scenario._min_image(s.mesh.yCell - Ly / 2, Ly)
+    r2 = dx ** 2 + dy ** 2
+    raw = np.zeros(s.mesh.nCells, np.int32)
+    raw[r2 <= 190e3 ** 2] = 1
+    raw[r2 <= 50e3 ** 2] = 2
+    with pytest.raises(fb.FbltsError) as e:
+        fb.mesh_regions(s.mesh, s.fVertex, raw, s.M, 0)
+    assert e.value.status == fb.E_REGIONS
+    want = scenario.enforce_level_separation(s.mesh, raw, min_sep=17)
+    assert not np.array_equal(want, raw)
+    got = np.zeros(s.mesh.nCells, np.int32)
+    for pair in range(2):
+        cc, _, _, _ = fb.mesh_regions(s.mesh, s.fVertex, raw, s.M, pair, promote=True)
+        got += (cc == fb.REGION_FINE).astype(np.int32)
+    np.testing.assert_array_equal(got, want)
