@@ -308,9 +308,11 @@ def timed_steps(fb, torch, st, stream, warm, k):
 def run_ensemble(args, rank):
     """Batched ensemble: `--members` shelf channels of seeded sizes (20k-800k
     cells), vortex tracks and M in {2, 4, 8}, FP32-tendency.  Times rounds of
-    one coarse step of every member, first in the plain form (each member's
-    own captured step, one instance per launch, on its own stream), then as a
-    batch (fblts_batch_*, launch shape tuned online)."""
+    one coarse step of every member in three forms, all with CUDA events:
+    plain concurrent (each member's captured step on its own stream, joined
+    per round), plain sequential (every member's captured step on one stream,
+    one instance per launch after another), and the batch (fblts_batch_*,
+    launch shape tuned online)."""
     if rank != 0:
         return
     import torch
@@ -318,61 +320,92 @@ def run_ensemble(args, rank):
     from synth import scenario
     torch.cuda.set_device(0)
     t0 = time.time()
-    states, cells, cu, Ms = [], 0, 0, []
     lo_c, hi_c = (int(x) for x in args.member_cells.split(","))
+    seq_stream = torch.cuda.Stream()
+    streams, states, seq_states, cells, cu, Ms, alg = [], [], [], 0, 0, [], 0.0
     for i in range(args.members):
         s = scenario.ensemble_member(i, n_min=lo_c, n_max=hi_c)
         mesh = fb.mesh_create(s.mesh, s.fVertex, level=s.level, M=s.M)
         fz = s.forcing
         vt = list(fz.vortex) + [float(np.mean(s.fVertex))] if fz.vortex is not None else None
-        p = fb.make_params(s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
-                           rho0=fz.rho0, rho_air=fz.rho_air, vortex=vt, precision=fb.FP32_TENDENCY, use_graph=True)
-        states.append(fb.state_init(mesh, p, s.h0, s.u0, s.bottom))
+
+        def params(stream):
+            return fb.make_params(s.dt, g=s.g, forcing=forcing_flags(s), wind=(fz.wind_u, fz.wind_v), cd=fz.cd,
+                                  rho0=fz.rho0, rho_air=fz.rho_air, vortex=vt, precision=fb.FP32_TENDENCY,
+                                  use_graph=True, stream=stream.cuda_stream)
+        streams.append(torch.cuda.Stream())
+        states.append(fb.state_init(mesh, params(streams[-1]), s.h0, s.u0, s.bottom))
+        seq_states.append(fb.state_init(mesh, params(seq_stream), s.h0, s.u0, s.bottom))
         cells += int(s.mesh.nCells)
         cu += int(mesh.info().cell_updates_per_step)
+        alg += fb.state_step_bytes(states[-1])[0]
         Ms.append(int(s.M[0]))
         del s
     setup_s = time.time() - t0
+    hbm, _ = peaks()
+    join = torch.cuda.Stream()
 
-    def sync_all():
-        for st in states:
-            fb.synchronize(st)
+    def concurrent_round():
+        fork = torch.cuda.Event()
+        fork.record(join)
+        for st, x in zip(states, streams):
+            x.wait_event(fork)
+            fb.lts_advance(st, 1)
+        for x in streams:
+            e = torch.cuda.Event()
+            e.record(x)
+            join.wait_event(e)
+
+    def timed(run, stream, k):
+        """per-round event times (ms) of k rounds on `stream`"""
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
         torch.cuda.synchronize()
+        evs[0].record(stream)
+        for r in range(k):
+            run()
+            evs[r + 1].record(stream)
+        torch.cuda.synchronize()
+        return [evs[r].elapsed_time(evs[r + 1]) for r in range(k)]
 
-    # plain: one member's captured coarse step per graph launch, members on their own streams
+    # plain, concurrent streams
     for _ in range(args.warmup):
-        for st in states:
+        concurrent_round()
+    conc = timed(concurrent_round, join, args.steps)
+    for st in states:
+        fb.synchronize(st)
+
+    # plain, sequential: one stream, one member's step after another
+    def sequential_round():
+        for st in seq_states:
             fb.lts_advance(st, 1)
-    sync_all()
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        for st in states:
-            fb.lts_advance(st, 1)
-    sync_all()
-    plain_s = time.perf_counter() - t
+    for _ in range(args.warmup):
+        sequential_round()
+    seq = timed(sequential_round, seq_stream, args.steps)
+    for st in seq_states:
+        fb.synchronize(st)
+        fb.state_destroy(st)
+
     # batched: tuning rounds, warm-up, then timed rounds with events on the batch stream
     stream = torch.cuda.Stream()
     b = fb.batch_create(states, autotune=True, stream=stream.cuda_stream)
     fb.batch_advance(b, 13)
     fb.batch_advance(b, args.warmup)
     fb.batch_synchronize(b)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(0) as clk:
-        torch.cuda.synchronize()
-        evs[0].record(stream)
-        for k in range(args.steps):
-            fb.batch_advance(b, 1)
-            evs[k + 1].record(stream)
-        fb.batch_synchronize(b)
-        torch.cuda.synchronize()
-    ms_total = evs[0].elapsed_time(evs[-1])
-    lat = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
+        lat = timed(lambda: fb.batch_advance(b, 1), stream, args.steps)
+    fb.batch_synchronize(b)
+    ms_round = sum(lat) / len(lat)
     info = fb.batch_info(b)
-    value = cu * args.steps / (ms_total / 1000.0)
-    plain = cu * args.steps / plain_s
+    value = cu / (ms_round / 1000.0)
+
+    def form(ts, launches):
+        ms = sum(ts) / len(ts)
+        return {"value": cu / (ms / 1000.0), "ms_per_round": ms, "step_hbm_frac": alg / (ms / 1000.0) / 1e9 / hbm,
+                "launches_per_round": launches, "timing": "CUDA events"}
+    lat = sorted(lat)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms_round, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32-tendency/f64-state", "data": "synthetic",
         "config": {"workload": "ensemble", "members": args.members, "member_cells": [lo_c, hi_c], "cells": cells,
                    "cell_updates_per_round": cu, "M": Ms,
@@ -380,9 +413,12 @@ def run_ensemble(args, rank):
                                   "seeded roughness and Holland vortex track, M in {2,4,8}; one round = one "
                                   "coarse step of every member", "parallelism": "single"},
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
-        "plain": {"value": plain, "ms_per_round": 1000.0 * plain_s / args.steps,
-                  "launches_per_round": int(info.member_launches_per_round), "timing": "host clock, device synced"},
-        "batched_vs_plain": value / plain,
+        "alg_bytes_per_round": alg,
+        "step_hbm_frac": alg / (ms_round / 1000.0) / 1e9 / hbm,
+        "plain_concurrent": form(conc, int(info.member_launches_per_round)),
+        "plain_sequential": form(seq, int(info.member_launches_per_round)),
+        "batched_vs_plain_concurrent": (sum(conc) / len(conc)) / ms_round,
+        "batched_vs_plain_sequential": (sum(seq) / len(seq)) / ms_round,
         "batch": {"mode": ("merged launches", "graph branches", "merged per group, groups as branches",
                            "merged per group of <= 4, groups as branches")[info.mode],
                   "groups": info.groups,
@@ -648,6 +684,7 @@ def main():
                      "traffic_over_alg": (traffic / (dbytes / max(dn, 1))) if (traffic and dbytes) else None,
                      "launches_per_step": dn, "share_of_step": dms / sum(v[0] for v in prof.values())},
         "profile_ms_per_step": {k: round(v[0], 4) for k, v in prof.items()},
+        "bytes_per_step_by_kind": {k: {"alg": v[0], "moved": v[1]} for k, v in bykind.items() if v[1] > 0},
         "gpu_launches": int(launches * args.steps + 1),
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": 8 * (nC + nE),
                 "d2h_bytes_per_step": 8 * (nC + nE), "steps": n_e2e},

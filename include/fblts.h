@@ -498,10 +498,13 @@ fblts_status fblts_batch_destroy(fblts_batch *batch);
  *
  * Requests are admitted first come, first served while the device bytes of
  * the running and finished-but-untaken states stay within hbm_budget (and
- * at most max_active run).  Each admitted request gets its own state, stream
- * and captured coarse step; the server issues steps_per_issue steps at a time
- * on that stream, so the running requests' work overlaps on the GPU, and a
- * request admitted while others run starts without waiting for them.
+ * at most max_active run).  Each admitted request gets its own state and
+ * captured coarse step; the server issues steps_per_issue steps at a time,
+ * so the running requests' work overlaps on the GPU, and a request admitted
+ * while others run starts without waiting for them.  Oldest first: the k-th
+ * oldest running request's steps go to a stream of the k-th highest stream
+ * priority the device offers, so the GPU favours older requests and younger
+ * ones take the capacity left (a request's steps stay in order).
  * fblts_server_progress does not block: call it in a loop.  The server
  * borrows the request's h0, u0, bottom until the request is admitted
  * (request_info status leaves 0), and its mesh until the request is taken

@@ -9,6 +9,12 @@
 // for a round to end, and a finished one frees its memory for the queue.
 // fblts_server_progress never blocks: it polls each running request's event,
 // issues its next steps, retires finished requests and admits queued ones.
+// Oldest first: each progress call ranks the running requests by admission
+// and issues request r's steps on a stream of the r-th highest priority (the
+// request's work stays ordered through its own event), so the GPU's block
+// scheduler favours the oldest requests' kernels and the younger ones fill
+// the remaining capacity: time-to-result stays close to first come, first
+// served, while the overlap still raises throughput.
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -40,6 +46,10 @@ struct Request {
 
 struct fblts_server {
     fblts_server_opts o{};
+    // issue streams by rank of age (rank 0 = oldest running request = the
+    // highest priority the device offers), created on demand
+    std::vector<cudaStream_t> rank_st;
+    int prio_least = 0, prio_greatest = 0;
     std::chrono::steady_clock::time_point t0;
     std::unordered_map<int64_t, Request> reqs;
     std::deque<int64_t> queue;
@@ -72,14 +82,57 @@ extern "C" fblts_status fblts_server_create(const fblts_server_opts *opts, fblts
     if (opts) srv->o = *opts;
     if (srv->o.steps_per_issue <= 0) srv->o.steps_per_issue = 1;
     if (srv->o.max_active < 0) { delete srv; set_error("server_create: max_active < 0"); return FBLTS_E_ARG; }
+    if (cudaDeviceGetStreamPriorityRange(&srv->prio_least, &srv->prio_greatest) != cudaSuccess) {
+        cudaGetLastError();
+        srv->prio_least = srv->prio_greatest = 0;
+    }
     srv->t0 = std::chrono::steady_clock::now();
     *out = srv;
     return FBLTS_OK;
 }
 
+// the issue stream of age rank k (priority greatest + k, clamped to least)
+static cudaStream_t rank_stream(fblts_server *srv, size_t k) {
+    while (srv->rank_st.size() <= k) {
+        const int r = (int)srv->rank_st.size();
+        const int prio = std::min(srv->prio_least, srv->prio_greatest + r);
+        cudaStream_t x = nullptr;
+        if (cudaStreamCreateWithPriority(&x, cudaStreamNonBlocking, prio) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        srv->rank_st.push_back(x);
+    }
+    return srv->rank_st[k];
+}
+
+// issues n coarse steps of request r on stream x after its earlier work, then
+// the state check, and records r.ev; the state's own stream waits for r.ev
+// so that later calls on the state (read, synchronize) see the steps
+static fblts_status issue(fblts_server *srv, Request &r, cudaStream_t x, int64_t n) {
+    fblts_state *s = r.st;
+    if (!x || !s->gexec) {
+        fblts_status st = fblts_lts_advance(s, n);
+        if (st == FBLTS_OK && cudaEventRecord(r.ev, s->st) != cudaSuccess) st = FBLTS_E_CUDA;
+        return st;
+    }
+    CK(cudaStreamWaitEvent(x, r.ev, 0));
+    for (int64_t i = 0; i < n; ++i) CK(cudaGraphLaunch(s->gexec, x));
+    CK(launch_check(s->arr.a[A_H], s->dm.bottom, s->mesh->hm.nC, s->arr.a[A_U], s->mesh->hm.nE, s->d_flag, x));
+    s->steps += n;
+    CK(cudaEventRecord(r.ev, x));
+    CK(cudaStreamWaitEvent(s->st, r.ev, 0));
+    (void)srv;
+    return FBLTS_OK;
+}
+
 extern "C" fblts_status fblts_server_destroy(fblts_server *srv) {
     if (!srv) return FBLTS_OK;
-    for (auto &kv : srv->reqs) release(srv, kv.second);
+    for (auto &kv : srv->reqs) {
+        if (kv.second.ev) cudaEventSynchronize(kv.second.ev);   // work issued on the rank streams
+        release(srv, kv.second);
+    }
+    for (cudaStream_t x : srv->rank_st) cudaStreamDestroy(x);
     delete srv;
     return FBLTS_OK;
 }
@@ -117,8 +170,9 @@ extern "C" fblts_status fblts_server_submit(fblts_server *srv, const fblts_reque
 extern "C" fblts_status fblts_server_progress(fblts_server *srv, int32_t *n_finished) {
     if (!srv) { set_error("server_progress: NULL server"); return FBLTS_E_ARG; }
     int32_t fin = 0;
-    // running requests: account the steps that completed, retire or issue more
+    // running requests, oldest first: account the steps that completed, retire or issue more
     std::vector<int64_t> still;
+    size_t rank = 0;
     for (int64_t k : srv->running) {
         Request &r = srv->reqs[k];
         bool active = true;
@@ -126,6 +180,7 @@ extern "C" fblts_status fblts_server_progress(fblts_server *srv, int32_t *n_fini
             const cudaError_t q = cudaEventQuery(r.ev);
             if (q == cudaErrorNotReady) {
                 still.push_back(k);
+                ++rank;
                 continue;
             }
             if (q != cudaSuccess) {
@@ -147,8 +202,7 @@ extern "C" fblts_status fblts_server_progress(fblts_server *srv, int32_t *n_fini
         }
         if (active) {
             const int64_t n = std::min<int64_t>(r.d.n_steps - r.done, srv->o.steps_per_issue);
-            fblts_status st = fblts_lts_advance(r.st, n);
-            if (st == FBLTS_OK && cudaEventRecord(r.ev, r.st->st) != cudaSuccess) st = FBLTS_E_CUDA;
+            fblts_status st = issue(srv, r, rank_stream(srv, rank), n);
             if (st != FBLTS_OK) {
                 r.status = RQ_FAILED;
                 r.err = st;
@@ -158,8 +212,12 @@ extern "C" fblts_status fblts_server_progress(fblts_server *srv, int32_t *n_fini
                 r.inflight = n;
             }
         }
-        if (active) still.push_back(k);
-        else ++fin;
+        if (active) {
+            still.push_back(k);
+            ++rank;
+        } else {
+            ++fin;
+        }
     }
     srv->running.swap(still);
     // admission, first come first served, while memory and the active cap allow
@@ -193,8 +251,9 @@ extern "C" fblts_status fblts_server_progress(fblts_server *srv, int32_t *n_fini
             continue;
         }
         const int64_t n = std::min<int64_t>(r.d.n_steps, srv->o.steps_per_issue);
-        st = fblts_lts_advance(r.st, n);
-        if (st == FBLTS_OK && cudaEventRecord(r.ev, r.st->st) != cudaSuccess) st = FBLTS_E_CUDA;
+        // the first issue follows the state's initialisation on its own stream
+        if (cudaEventRecord(r.ev, r.st->st) != cudaSuccess) st = FBLTS_E_CUDA;
+        if (st == FBLTS_OK) st = issue(srv, r, rank_stream(srv, srv->running.size()), n);
         if (st != FBLTS_OK) {
             r.status = RQ_FAILED;
             r.err = st;
