@@ -45,6 +45,8 @@ def make_workload(name, build=True):
                   "closed basin, variable-resolution Voronoi mesh (~2.0M cells): 500 m along a seeded sinuous "
                   "coast growing to 20 km offshore, depth 5-4000 m, 3 LTS levels (M=8) by gravity-wave CFL, "
                   "moving Holland vortex with wind stress, pressure gradient and quadratic drag"),
+        "basin_half": (lambda: basin.basin_case(Ly=4800e3),
+                       "1/2-length sample of the basin workload (same recipe, Ly 4800 km, ~1.0M cells)"),
         "basin_small": (lambda: basin.basin_case(Ly=1200e3),
                         "1/8-length sample of the basin workload (same recipe, Ly 1200 km, ~0.25M cells)"),
         "basin_tiny": (lambda: basin.basin_case(Ly=150e3),

@@ -129,6 +129,17 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     addi(hm.nEoE, &dm.nEoE);
     addi(slot_major(hm.eoe, nE, mE2), &dm.eoe);
     addd(slot_major(hm.woe, nE, mE2), &dm.woe);
+    {   // the FP64 path's TRiSK weights as double-float pairs: hi = nearest float, lo = the rest
+        std::vector<float> wdf((size_t)2 * nE * mE2);
+        const std::vector<double> w = slot_major(hm.woe, nE, mE2);
+        for (size_t k = 0; k < w.size(); ++k) {
+            const float hi = (float)w[k];
+            wdf[2 * k] = hi;
+            wdf[2 * k + 1] = (float)(w[k] - (double)hi);
+        }
+        fkeep.emplace_back(std::move(wdf));
+        items.push_back({fkeep.back().data(), fkeep.back().size() * sizeof(float), (void **)&dm.woeDF});
+    }
     addd(hm.invDc, &dm.invDc);
     bkeep.push_back(hm.ebnd);
     items.push_back({bkeep.back().data(), bkeep.back().size(), (void **)&dm.ebnd});

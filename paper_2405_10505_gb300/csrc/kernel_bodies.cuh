@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cmath>
+#include <cstring>
 
 #include "kernels.cuh"
 
@@ -41,16 +42,22 @@ struct VertArgs {
     double *q;
 };
 
+// FP64 edge prep: per edge q_e (double) and, for the neighbour sums of the
+// edge pass, {F, F q_e} and u as double-float pairs (rec, udf)
 struct PrepArgs {
     int lo, hi;
     const double *u_in, *hst, *q;
-    double *Fe, *qe, *FQ;
+    double *qe;
+    float4 *rec;
+    float2 *udf;
 };
 
 struct EdgeArgs {
     SegSet segs;
     int lo, hi;
-    const double *u_in, *hst, *K, *Fe, *qe, *FQ, *u0;
+    const double *u_in, *hst, *K, *qe, *u0;
+    const float4 *rec;
+    const float2 *udf;
     double *us_out, *u_state, *acc;
     const double *slow;   // splitting: the slow part of Phi per edge
     double cdt, g;
@@ -90,7 +97,10 @@ inline VertArgs vert_args(const Op &op, const DevArrays &arr) {
 }
 
 inline PrepArgs prep_args(const Op &op, const DevArrays &arr) {
-    return PrepArgs{op.lo, op.hi, arr.a[op.in_u], arr.a[op.hst], arr.a[A_Q], arr.a[A_FE], arr.a[A_QE], arr.a[A_FQ]};
+    // the double-float records live in the A_FQU area (16 bytes per edge) and
+    // the split velocity in the A_FE area (8 bytes per edge)
+    return PrepArgs{op.lo, op.hi, arr.a[op.in_u], arr.a[op.hst], arr.a[A_Q], arr.a[A_QE], (float4 *)arr.a[A_FQU],
+                    (float2 *)arr.a[A_FE]};
 }
 
 inline EdgeArgs edge_args(const Op &op, const DevArrays &arr, double g) {
@@ -98,7 +108,8 @@ inline EdgeArgs edge_args(const Op &op, const DevArrays &arr, double g) {
     EdgeArgs a;
     a.segs = segs_of(op);
     a.lo = op.lo; a.hi = op.hi;
-    a.u_in = A[op.in_u]; a.hst = A[op.hst]; a.K = A[A_K]; a.Fe = A[A_FE]; a.qe = A[A_QE]; a.FQ = A[A_FQ];
+    a.u_in = A[op.in_u]; a.hst = A[op.hst]; a.K = A[A_K]; a.qe = A[A_QE];
+    a.rec = (const float4 *)A[A_FQU]; a.udf = (const float2 *)A[A_FE];
     a.u0 = A[op.u0]; a.us_out = A[op.out_u]; a.u_state = A[A_U]; a.acc = A[A_ACCU];
     a.slow = A[A_SLOW];
     a.cdt = op.cdt; a.g = g;
@@ -120,6 +131,138 @@ inline IfArgs if_args(const Op &op, const DevArrays &arr) {
     a.acch = A[A_ACCH]; a.accu = A[A_ACCU];
     a.k = op.k; a.M = op.Mk; a.b1 = op.fb_a; a.b2 = op.fb_b; a.b3 = op.fb_c; a.cf = op.cdt;
     return a;
+}
+
+// ---------------------------------------------------------------- double-float
+// GB300 issues FP64 at 1/64 of its FP32 rate.  The FP64 path therefore takes
+// its edgesOnEdge sums on the FP32 pipe in double-float arithmetic: a value
+// is the unevaluated sum hi + lo of two floats (about 48 significant bits),
+// products are exact through Dekker's product with a fused multiply-add
+// (the rounding error of a*b is fma(a, b, -a*b)) and sums through Knuth's
+// TwoSum (the error of s = a + b is (a - (s - bb)) + (b - bb), bb = s - a).
+// Conversions between double and float pairs go through the bit patterns on
+// the integer pipe: GB300's float/double conversion instructions cost about
+// as much as an FP64 operation.
+
+FB_HD unsigned long long fb_bits(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long b;
+    std::memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+FB_HD double fb_from_bits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double x;
+    std::memcpy(&x, &b, sizeof x);
+    return x;
+#endif
+}
+FB_HD unsigned fb_fbits(float x) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(x);
+#else
+    unsigned b;
+    std::memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+FB_HD float fb_ffrom_bits(unsigned b) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float x;
+    std::memcpy(&x, &b, sizeof x);
+    return x;
+#endif
+}
+
+// x truncated to a float (sign, exponent, top 23 mantissa bits); 0 below the
+// smallest normal float; infinities and NaN stay infinite / NaN
+FB_HD float df_trunc(double x) {
+    const unsigned long long b = fb_bits(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const int ed = (int)((hw >> 20) & 0x7FFu);
+    const unsigned sign = hw & 0x80000000u;
+    const unsigned m = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    if (ed == 0x7FF) return fb_ffrom_bits(sign | 0x7F800000u | (m ? 1u : 0u));
+    const int e = ed - 1023 + 127;
+    if (e <= 0) return fb_ffrom_bits(sign);
+    if (e >= 255) return fb_ffrom_bits(sign | 0x7F800000u);
+    return fb_ffrom_bits(sign | ((unsigned)e << 23) | m);
+}
+
+// the double value of a float (exact; subnormal floats become 0)
+FB_HD double df_widen(float f) {
+    const unsigned u = fb_fbits(f);
+    const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e == 0) return fb_from_bits(sign);
+    const unsigned long long ed = e == 0xFFu ? 0x7FFull : (unsigned long long)(e - 127 + 1023);
+    return fb_from_bits(sign | (ed << 52) | ((unsigned long long)m << 29));
+}
+
+// x as hi + lo: hi is x with the low 29 mantissa bits cleared (a float
+// exactly), lo = x - hi (exact in double) truncated to a float; relative
+// error at most 2^-47
+FB_HD float2 df_split(double x) {
+    const double hi = fb_from_bits(fb_bits(x) & ~((1ull << 29) - 1ull));
+    return make_float2(df_trunc(hi), df_trunc(x - hi));
+}
+
+FB_HD double df_value(float2 s) { return df_widen(s.x) + df_widen(s.y); }
+
+// s += a * b in double-float (the lo * lo term, 2^-48 of the product, dropped)
+FB_HD void df_fma(float2 &s, float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    const float ph = __fmul_rn(a.x, b.x);
+    float pl = fmaf(a.x, b.x, -ph);
+    pl = fmaf(a.x, b.y, fmaf(a.y, b.x, pl));
+    const float t = __fadd_rn(s.x, ph);
+    const float bb = __fsub_rn(t, s.x);
+    const float err = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fsub_rn(ph, bb));
+    s.y = __fadd_rn(s.y, __fadd_rn(err, pl));
+#else
+    const float ph = a.x * b.x;
+    float pl = std::fmaf(a.x, b.x, -ph);
+    pl = std::fmaf(a.x, b.y, std::fmaf(a.y, b.x, pl));
+    const float t = s.x + ph;
+    const float bb = t - s.x;
+    const float err = (s.x - (t - bb)) + (ph - bb);
+    s.y = s.y + (err + pl);
+#endif
+    s.x = t;
+}
+
+// 1/x for finite x > 0: a float estimate refined by two Newton steps on
+// f(r) = 1/r - x (r <- r + r (1 - x r)), each about doubling the correct bits
+FB_HD double rcp_nr(double x) {
+#ifdef __CUDA_ARCH__
+    double r = df_widen(__fdividef(1.0f, df_trunc(x)));
+#else
+    double r = df_widen(1.0f / df_trunc(x));
+#endif
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
+// sqrt(a) for a >= 0: a y with y = 1/sqrt(a) from a float estimate and one
+// Newton step on f(y) = 1/y^2 - a (y <- y (3 - a y^2) / 2), a relative error
+// of about 2^-44; 0 for a below the smallest normal float
+FB_HD double sqrt_nr(double a) {
+    const float af = df_trunc(a);
+    if (!(af > 0.0f)) return 0.0;
+#ifdef __CUDA_ARCH__
+    const double y = df_widen(rsqrtf(af));
+#else
+    const double y = df_widen(1.0f / std::sqrt(af));
+#endif
+    const double ay = a * y;
+    return ay * fma(-0.5 * ay, y, 1.5);
 }
 
 // ---------------------------------------------------------------- bodies
@@ -180,7 +323,8 @@ FB_HD void cell_body(const DevMesh &m, const CellArgs &a, int i) {
 }
 
 // Vertex v: zeta_v = sum_j t_{e,v} d_e u_e / A_v, h_v = H_v + sum_j kite xi / A_v,
-// q_v = (zeta_v + f_v) / h_v  (Eq. trisk_vorticity; PV q = eta / h).
+// q_v = (zeta_v + f_v) / h_v  (Eq. trisk_vorticity; PV q = eta / h); the
+// division through rcp_nr.
 FB_HD void vert_body(const DevMesh &m, const VertArgs &a, int v) {
     const int nV = m.nV;
     double z = 0.0, hv = m.Hv64[v];
@@ -189,19 +333,22 @@ FB_UNROLL
         z += m.cVort[j * nV + v] * a.u_in[m.eov[j * nV + v]];
         hv += m.cKite[j * nV + v] * a.hst[m.cov[j * nV + v]];
     }
-    a.q[v] = (z + m.fV[v]) / hv;
+    a.q[v] = (z + m.fV[v]) * rcp_nr(hv);
 }
 
 // Edge e: thickness flux F_e = h_e u_e with h_e = H_e + (xi_c0 + xi_c1)/2
 // (zero on no-flow edges), the edge PV q_e = (q_v0 + q_v1) / 2 and their
-// product F_e q_e.
+// product F_e q_e, in double; F_e, F_e q_e and u_e are stored as
+// double-float pairs for the edge pass's neighbour sums.
 FB_HD void prep_body(const DevMesh &m, const PrepArgs &a, int e) {
     const int c0 = m.coe0[e], c1 = m.coe1[e];
-    const double F = m.ebnd[e] ? 0.0 : (m.He64[e] + 0.5 * (a.hst[c0] + a.hst[c1])) * a.u_in[e];
+    const double u = a.u_in[e];
+    const double F = m.ebnd[e] ? 0.0 : (m.He64[e] + 0.5 * (a.hst[c0] + a.hst[c1])) * u;
     const double q = 0.5 * (a.q[m.voe0[e]] + a.q[m.voe1[e]]);
-    a.Fe[e] = F;
     a.qe[e] = q;
-    a.FQ[e] = F * q;
+    const float2 f = df_split(F), g = df_split(F * q);
+    a.rec[e] = make_float4(f.x, f.y, g.x, g.y);
+    a.udf[e] = df_split(u);
 }
 
 // Edge e: Phi_e = sum_j w_j F_{e_j} (q_e + q_{e_j}) / 2
@@ -210,7 +357,10 @@ FB_HD void prep_body(const DevMesh &m, const PrepArgs &a, int e) {
 // (rotating SWE, Eq. nonlinear_swe, in TRiSK form; forcing of Eq.
 // hurricane_model), then the stage update u_s = u0 + c tau Phi or the
 // correction sum of Eq. if_correction.  The Coriolis sum is taken as
-// (q_e sum_j w_j F_j + sum_j w_j F_j q_j) / 2: two FMAs per neighbour.
+// (q_e sum_j w_j F_j + sum_j w_j F_j q_j) / 2; the two sums over the
+// edgesOnEdge list and the tangential velocity sum_j w_j u_j run in
+// double-float on the FP32 pipe (df_fma), the rest in double, with the
+// forcing's square roots and reciprocal by Newton steps (sqrt_nr, rcp_nr).
 template <bool FORCING>
 FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, int e) {
     const int mode = seg_mode(a.segs, e);
@@ -226,27 +376,29 @@ FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, 
         const int c0 = m.coe0[e], c1 = m.coe1[e];
         const int n = m.nEoE[e];
         const double qself = a.qe[e];
-        double sF = 0.0, sG = 0.0, vt = 0.0;
+        float2 sF = make_float2(0.f, 0.f), sG = sF, sv = sF;
         for (int j = 0; j < n; ++j) {
             const int x = m.eoe[j * nE + e];
-            const double w = m.woe[j * nE + e];
-            sF += w * a.Fe[x];
-            sG += w * a.FQ[x];
-            if (FORCING) vt += w * a.u_in[x];
+            const float2 w = m.woeDF[j * nE + e];
+            const float4 r = a.rec[x];
+            df_fma(sF, w, make_float2(r.x, r.y));
+            df_fma(sG, w, make_float2(r.z, r.w));
+            if (FORCING) df_fma(sv, w, a.udf[x]);
         }
-        const double cor = 0.5 * (qself * sF + sG);
+        const double cor = 0.5 * (qself * df_value(sF) + df_value(sG));
         const double h0c = a.hst[c0], h1c = a.hst[c1];
         const double gg = a.split == 1 ? 0.0 : a.g;   // the slow terms leave gravity out
         const double grad = (a.K[c1] - a.K[c0]) + gg * (h1c - h0c);
         phi = cor - grad * m.invDc[e];
         if (FORCING) {
             const double ue = a.u_in[e];
-            const double rhe = 1.0 / (m.He64[e] + 0.5 * (h0c + h1c));
+            const double vt = df_value(sv);
+            const double rhe = rcp_nr(m.He64[e] + 0.5 * (h0c + h1c));
             if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
                 const double dn = fz.windN[e] - ue, dt = fz.windT[e] - vt;
-                phi += fz.cw[e] * sqrt(dn * dn + dt * dt) * dn * rhe;
+                phi += fz.cw[e] * sqrt_nr(dn * dn + dt * dt) * dn * rhe;
             }
-            if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= fz.cd * sqrt(ue * ue + vt * vt) * ue * rhe;
+            if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= fz.cd * sqrt_nr(ue * ue + vt * vt) * ue * rhe;
             if (fz.flags & FBLTS_FORCE_VORTEX) phi -= (fz.ps[c1] - fz.ps[c0]) * m.invDc[e] / fz.rho0;
         }
     }

@@ -17,6 +17,7 @@ struct DevMesh {
     const int *coe0, *coe1, *voe0, *voe1;  // edges
     const int *nEoE, *eoe;
     const double *woe, *invDc;
+    const float2 *woeDF;                // FP64 path: W as a double-float pair (hi, lo), slot-major
     const unsigned char *ebnd;
     const double *cosE, *sinE, *xE, *yE, *xC, *yC;
     const int *eov, *cov;               // vertices
