@@ -361,6 +361,10 @@ enum {
 };
 fblts_status fblts_plan_op(const fblts_mesh_desc *desc, const fblts_params *params, int64_t index,
                            int32_t *kind, int32_t *stage, uint8_t *mode);
+/* The algorithmic and moved bytes (the models of fblts_state_bytes_by_kind)
+ * of op `index` of that launch list, host only; either pointer may be NULL. */
+fblts_status fblts_plan_op_bytes(const fblts_mesh_desc *desc, const fblts_params *params, int64_t index,
+                                 double *alg_bytes, double *moved_bytes);
 fblts_status fblts_state_profile_step(fblts_state *state, double *ms, int64_t *launches,
                                       double *alg_bytes);
 

@@ -104,7 +104,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_TAKEN = range(5)
 _LIB = None
 SYMBOLS = ("fblts_last_error", "fblts_mesh_create", "fblts_mesh_destroy", "fblts_mesh_get_info", "fblts_mesh_regions",
            "fblts_mesh_levels",
-           "fblts_plan_step", "fblts_plan_op",
+           "fblts_plan_step", "fblts_plan_op", "fblts_plan_op_bytes",
            "fblts_state_init", "fblts_state_destroy", "fblts_lts_advance", "fblts_synchronize",
            "fblts_state_read", "fblts_state_write", "fblts_run_host", "fblts_diagnostics",
            "fblts_state_time", "fblts_state_save", "fblts_state_load", "fblts_state_launches_per_step",
@@ -141,6 +141,7 @@ def lib():
                                 C.POINTER(C.c_int64)],
             "fblts_plan_op": [C.POINTER(MeshDesc), C.POINTER(Params), C.c_int64, C.POINTER(C.c_int32),
                               C.POINTER(C.c_int32), C.POINTER(C.c_uint8)],
+            "fblts_plan_op_bytes": [C.POINTER(MeshDesc), C.POINTER(Params), C.c_int64, _PD, _PD],
             "fblts_state_init": [V, C.POINTER(Params), _PD, _PD, _PD, C.POINTER(V)],
             "fblts_state_destroy": [V],
             "fblts_lts_advance": [V, C.c_int64],
@@ -284,6 +285,14 @@ def plan_op(m, fVertex, level, M, params, index, nIF1=0, nIF2=0):
     n = {"cell": m.nCells, "trisk": m.nCells, "vertex": m.nVertices, "edge": m.nEdges,
          "edge_prep": m.nEdges}.get(name)
     return name, int(st.value), (buf[: int(n)].copy() if n is not None else None)
+
+
+def plan_op_bytes(m, fVertex, level, M, params, index, nIF1=0, nIF2=0):
+    """fblts_plan_op_bytes (host only): (algorithmic, moved) bytes of op ``index``."""
+    d, keep = _mesh_desc(m, fVertex, level, M, nIF1, nIF2)
+    a, mv = C.c_double(), C.c_double()
+    _check(lib().fblts_plan_op_bytes(C.byref(d), C.byref(params), int(index), C.byref(a), C.byref(mv)))
+    return float(a.value), float(mv.value)
 
 
 def _mesh_desc(m, fVertex, level, M, nIF1, nIF2, promote=False):

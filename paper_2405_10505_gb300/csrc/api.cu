@@ -631,6 +631,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     fz.flags = p->forcing;
     fz.wind_u = p->wind_u; fz.wind_v = p->wind_v; fz.cd = p->cd;
     fz.rho0 = p->rho0 > 0 ? p->rho0 : 1025.0;
+    fz.inv_rho0 = 1.0 / fz.rho0;
     fz.rho_air = p->rho_air > 0 ? p->rho_air : 1.225;
     for (int k = 0; k < 9; ++k) fz.vx[k] = p->vortex[k];
     fz.t0 = p->t0; fz.dt = p->dt; fz.step = s->d_step;
@@ -840,6 +841,21 @@ extern "C" fblts_status fblts_plan_op(const fblts_mesh_desc *desc, const fblts_p
             mode[n2o[x]] = (uint8_t)m;
         }
     }
+    return FBLTS_OK;
+}
+
+extern "C" fblts_status fblts_plan_op_bytes(const fblts_mesh_desc *desc, const fblts_params *p, int64_t index,
+                                           double *alg_bytes, double *moved_bytes) {
+    HostMesh hm;
+    Schedule s;
+    const fblts_status st = plan(desc, p, "plan_op_bytes", hm, s);
+    if (st != FBLTS_OK) return st;
+    if (index < 0 || index >= (int64_t)s.ops.size()) {
+        set_error("plan_op_bytes: index %lld outside [0, %zu)", (long long)index, s.ops.size());
+        return FBLTS_E_ARG;
+    }
+    if (alg_bytes) *alg_bytes = s.ops[(size_t)index].alg_bytes;
+    if (moved_bytes) *moved_bytes = s.ops[(size_t)index].moved_bytes;
     return FBLTS_OK;
 }
 

@@ -250,19 +250,61 @@ FB_HD double rcp_nr(double x) {
     return fma(r, fma(-x, r, 1.0), r);
 }
 
-// sqrt(a) for a >= 0: a y with y = 1/sqrt(a) from a float estimate and one
-// Newton step on f(y) = 1/y^2 - a (y <- y (3 - a y^2) / 2), a relative error
-// of about 2^-44; 0 for a below the smallest normal float
-FB_HD double sqrt_nr(double a) {
-    const float af = df_trunc(a);
-    if (!(af > 0.0f)) return 0.0;
+// Double-float operations for the FP64 edge pass's forcing terms (the same
+// error-free transformations; each result normalised so |lo| <= ulp(hi)/2,
+// relative error about 2^-46).  Rounded float operations that the compiler
+// may not contract: fadd_ / fsub_ / fmul_.
 #ifdef __CUDA_ARCH__
-    const double y = df_widen(rsqrtf(af));
+#define FF_ADD(a, b) __fadd_rn((a), (b))
+#define FF_SUB(a, b) __fsub_rn((a), (b))
+#define FF_MUL(a, b) __fmul_rn((a), (b))
 #else
-    const double y = df_widen(1.0f / std::sqrt(af));
+#define FF_ADD(a, b) ((a) + (b))
+#define FF_SUB(a, b) ((a) - (b))
+#define FF_MUL(a, b) ((a) * (b))
 #endif
-    const double ay = a * y;
-    return ay * fma(-0.5 * ay, y, 1.5);
+
+// s + e with |e| small against s (Dekker's Fast2Sum)
+FB_HD float2 ff_norm(float s, float e) {
+    const float h = FF_ADD(s, e);
+    return make_float2(h, FF_SUB(e, FF_SUB(h, s)));
+}
+
+FB_HD float2 ff_add(float2 a, float2 b) {
+    const float s = FF_ADD(a.x, b.x);
+    const float bb = FF_SUB(s, a.x);
+    const float e = FF_ADD(FF_SUB(a.x, FF_SUB(s, bb)), FF_SUB(b.x, bb));
+    return ff_norm(s, FF_ADD(e, FF_ADD(a.y, b.y)));
+}
+
+FB_HD float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+FB_HD float2 ff_mul(float2 a, float2 b) {
+    const float p = FF_MUL(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    return ff_norm(p, e);
+}
+
+// sqrt(a) for a >= 0: the float root s refined by one Newton step with the
+// exact residual a - s^2 (fma); 0 for a <= 0
+FB_HD float2 ff_sqrt(float2 a) {
+    if (!(a.x > 0.f)) return make_float2(0.f, 0.f);
+#ifdef __CUDA_ARCH__
+    const float s = __fsqrt_rn(a.x);
+#else
+    const float s = std::sqrt(a.x);
+#endif
+    const float r = FF_ADD(fmaf(-s, s, a.x), a.y);
+    return ff_norm(s, FF_MUL(r, FF_MUL(0.5f, 1.0f / s)));
+}
+
+// 1/a for a > 0: the float reciprocal refined by one Newton step with the
+// exact residual 1 - a r (fma)
+FB_HD float2 ff_rcp(float2 a) {
+    const float r = 1.0f / a.x;
+    const float e = FF_SUB(fmaf(-a.x, r, 1.0f), FF_MUL(a.y, r));
+    return ff_norm(r, FF_MUL(r, e));
 }
 
 // ---------------------------------------------------------------- bodies
@@ -359,8 +401,9 @@ FB_HD void prep_body(const DevMesh &m, const PrepArgs &a, int e) {
 // correction sum of Eq. if_correction.  The Coriolis sum is taken as
 // (q_e sum_j w_j F_j + sum_j w_j F_j q_j) / 2; the two sums over the
 // edgesOnEdge list and the tangential velocity sum_j w_j u_j run in
-// double-float on the FP32 pipe (df_fma), the rest in double, with the
-// forcing's square roots and reciprocal by Newton steps (sqrt_nr, rcp_nr).
+// double-float on the FP32 pipe (df_fma), and so do the wind stress and
+// drag (ff_*); the pressure, kinetic-energy and vortex-pressure gradients
+// and the update stay in double.
 template <bool FORCING>
 FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, int e) {
     const int mode = seg_mode(a.segs, e);
@@ -391,15 +434,24 @@ FB_HD void edge_body(const DevMesh &m, const EdgeArgs &a, const DevForcing &fz, 
         const double grad = (a.K[c1] - a.K[c0]) + gg * (h1c - h0c);
         phi = cor - grad * m.invDc[e];
         if (FORCING) {
-            const double ue = a.u_in[e];
-            const double vt = df_value(sv);
-            const double rhe = rcp_nr(m.He64[e] + 0.5 * (h0c + h1c));
+            // wind stress and quadratic drag in double-float: u_e from the edge
+            // prep's pair, v_e = sum_j w_j u_j from the sum above
+            const float2 ue = a.udf[e];
+            const float2 vt = ff_norm(sv.x, sv.y);
+            const float2 rhe = ff_rcp(df_split(m.He64[e] + 0.5 * (h0c + h1c)));
+            float2 f = make_float2(0.f, 0.f);
             if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
-                const double dn = fz.windN[e] - ue, dt = fz.windT[e] - vt;
-                phi += fz.cw[e] * sqrt_nr(dn * dn + dt * dt) * dn * rhe;
+                const float2 dn = ff_add(df_split(fz.windN[e]), ff_neg(ue));
+                const float2 dt = ff_add(df_split(fz.windT[e]), ff_neg(vt));
+                const float2 mag = ff_sqrt(ff_add(ff_mul(dn, dn), ff_mul(dt, dt)));
+                f = ff_mul(ff_mul(df_split(fz.cw[e]), mag), ff_mul(dn, rhe));
             }
-            if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= fz.cd * sqrt_nr(ue * ue + vt * vt) * ue * rhe;
-            if (fz.flags & FBLTS_FORCE_VORTEX) phi -= (fz.ps[c1] - fz.ps[c0]) * m.invDc[e] / fz.rho0;
+            if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) {
+                const float2 sp = ff_sqrt(ff_add(ff_mul(ue, ue), ff_mul(vt, vt)));
+                f = ff_add(f, ff_neg(ff_mul(ff_mul(df_split(fz.cd), sp), ff_mul(ue, rhe))));
+            }
+            phi += df_value(f);
+            if (fz.flags & FBLTS_FORCE_VORTEX) phi -= (fz.ps[c1] - fz.ps[c0]) * m.invDc[e] * fz.inv_rho0;
         }
     }
     switch (mode) {

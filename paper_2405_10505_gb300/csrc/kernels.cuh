@@ -59,6 +59,7 @@ struct DevForcing {
     float4 *wrec32;
     float *ps32;
     double wind_u, wind_v, cd, rho0, rho_air;
+    double inv_rho0;           // 1 / rho0 (the per-edge pressure force multiplies by it)
     double vx[9];
     double t0, dt;
     const long long *step;     // device step counter

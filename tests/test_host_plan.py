@@ -166,3 +166,26 @@ def test_correction_sums_cover_if1_and_if2(name):
             assert len(got) == steps[p] * s.M[p]
             assert got.count(fb.SEG_SUM_SET) == steps[p]
             assert all(got[j] == (fb.SEG_SUM_SET if j % s.M[p] == 0 else fb.SEG_SUM_ADD) for j in range(len(got)))
+
+
+def test_op_bytes_add_up_to_the_step():
+    """The per-op algorithmic bytes sum to fblts_plan_step's total; the moved
+    count is never below the algorithmic one, and only the FP32 path's TRiSK
+    and edge passes (the per-slot shares) and the padded-row cell pass move
+    more than the arithmetic needs."""
+    s = CASES["nested_3level"]()
+    for prec in (fb.FP64, fb.FP32_TENDENCY):
+        p = fb.make_params(s.dt, precision=prec)
+        n, total, _ = fb.plan_step(s.mesh, s.fVertex, s.level, s.M, p)
+        alg = moved = 0.0
+        for i in range(n):
+            a, mv = fb.plan_op_bytes(s.mesh, s.fVertex, s.level, s.M, p, i)
+            kind = fb.plan_op(s.mesh, s.fVertex, s.level, s.M, p, i)[0]
+            assert mv >= a >= 0.0
+            if mv > a:
+                assert (prec == fb.FP32_TENDENCY and kind in ("trisk", "edge", "cell")) or \
+                    (prec == fb.FP64 and kind == "cell"), (prec, kind)
+            alg += a
+            moved += mv
+        assert abs(alg - total) <= 1e-9 * total
+        assert moved >= alg
