@@ -149,7 +149,14 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     if (mode == SEG_NONE) return;
     const int n = m.nEoC[i];
     int er[NMAX], nb[NMAX];
-    float ue[NMAX], sdv[NMAX], kw[NMAX], He[NMAX];
+    float ue[NMAX], sdv[NMAX], kw[NMAX], He[NMAX], xn[NMAX];
+    // every load the cell needs is issued in one round after the row: the
+    // cell's own values first, the slot gathers (u, edge record, neighbour xi)
+    // together, so no gather waits on an earlier one's arithmetic
+    const float xi_i = a.xi_in[i];
+    const float x0 = a.xi0[i];
+    const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;   // the stage-2 value enters stage 3 only
+    const double invA = m.invA[i];
     if constexpr (ROWS) {
         // cell-major rows padded with valid indices: vector loads, then the
         // gathers of the first ROW_MAIN slots unconditionally (padding masked)
@@ -168,10 +175,12 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
             kw[j] = 0.f;
             He[j] = 0.f;
             sdv[j] = 0.f;
+            xn[j] = 0.f;
             if (j < ROW_MAIN || n > ROW_MAIN) {   // slots past ROW_MAIN only for cells that have them
                 const int e = er[j] < 0 ? ~er[j] : er[j];
                 const float u = a.u_in[e];
                 const float4 st = m.estat[e];
+                xn[j] = a.xi_in[nb[j]];
                 ue[j] = j < n ? u : 0.f;
                 kw[j] = st.y;
                 He[j] = st.z;
@@ -195,9 +204,11 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
             sdv[j] = 0.f;
             kw[j] = 0.f;
             He[j] = 0.f;
+            xn[j] = 0.f;
             if (j < n) {
                 const int e = er[j] < 0 ? ~er[j] : er[j];
                 ue[j] = a.u_in[e];
+                xn[j] = a.xi_in[nb[j]];
                 const float4 st = m.estat[e];
                 kw[j] = st.y;
                 He[j] = st.z;
@@ -208,23 +219,19 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     float ke = 0.f;
     FB_UNROLL
     for (int j = 0; j < NMAX; ++j) ke += kw[j] * ue[j] * ue[j];
-    const double invA = m.invA[i];
     a.K[i] = ke * (float)invA;
     if (mode == SEG_KONLY) return;
-    const float xi_i = a.xi_in[i];
     float F[NMAX];
     FB_UNROLL
     for (int j = 0; j < NMAX; ++j)
-        F[j] = (!ROWS || j < ROW_MAIN || n > ROW_MAIN) ? (He[j] + 0.5f * (xi_i + a.xi_in[nb[j]])) * ue[j] : 0.f;
+        F[j] = (!ROWS || j < ROW_MAIN || n > ROW_MAIN) ? (He[j] + 0.5f * (xi_i + xn[j])) * ue[j] : 0.f;
     if (mode == SEG_UPD || mode == SEG_RK_SET || mode == SEG_RK_ADD2) {
         float S = 0.f;
         FB_UNROLL
         for (int j = 0; j < NMAX; ++j) S += sdv[j] * F[j];
-        const float x0 = a.xi0[i];
-        const float xn = x0 + (float)a.cdt * (S * (float)invA);
-        a.xi_out[i] = xn;
-        const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;   // the stage-2 value enters stage 3 only
-        a.hst_out[i] = a.fb_a * xn + a.fb_b * xp + a.fb_c * x0;
+        const float xs = x0 + (float)a.cdt * (S * (float)invA);
+        a.xi_out[i] = xs;
+        a.hst_out[i] = a.fb_a * xs + a.fb_b * xp + a.fb_c * x0;
         if (mode == SEG_UPD) return;
     }
     double S = 0.0;
@@ -233,26 +240,22 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     const double psi = S * invA;
     switch (mode) {
         case SEG_INPLACE: {
-            const float x0 = a.xi0[i];
             const double hn = a.h_state[i] + a.cdt * psi;
-            const float xn = (float)hn;
+            const float xs = (float)hn;
             a.h_state[i] = hn;
-            a.xi_shadow[i] = xn;
-            const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;   // the stage-2 value enters stage 3 only
-            a.hst_out[i] = a.fb_a * xn + a.fb_b * xp + a.fb_c * x0;
+            a.xi_shadow[i] = xs;
+            a.hst_out[i] = a.fb_a * xs + a.fb_b * xp + a.fb_c * x0;
         } break;
         case SEG_ACC_SET: a.acc[i] = psi; break;
         case SEG_ACC_ADD: a.acc[i] += psi; break;
         case SEG_RK_SET: a.acc[i] = psi; break;          // RK4: the tendency sum in double
         case SEG_RK_ADD2: a.acc[i] += 2.0 * psi; break;
         case SEG_RK_FIN: {
-            const float x0 = a.xi0[i];
             const double hn = a.h_state[i] + a.cdt * (a.acc[i] + psi);
-            const float xn = (float)hn;
+            const float xs = (float)hn;
             a.h_state[i] = hn;
-            a.xi_shadow[i] = xn;
-            const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;
-            a.hst_out[i] = a.fb_a * xn + a.fb_b * xp + a.fb_c * x0;
+            a.xi_shadow[i] = xs;
+            a.hst_out[i] = a.fb_a * xs + a.fb_b * xp + a.fb_c * x0;
         } break;
         default: break;
     }
