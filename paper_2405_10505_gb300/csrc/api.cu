@@ -182,6 +182,7 @@ extern "C" fblts_status fblts_mesh_create(const fblts_mesh_desc *desc, fblts_mes
     addf(hm.dvE, &dm.dv32);
     addf(hm.keE, &dm.ke32);
     addd(hm.invA, &dm.invA);
+    addf(hm.invA, &dm.invA32);
     dm.rowS = hm.rows_canonical ? hm.rowS : 0;
     if (dm.rowS) {
         addi(hm.rowE, &dm.rowE);
@@ -629,7 +630,7 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     DevForcing &fz = s->fz;
     fz.fp32 = f32 ? 1 : 0;
     fz.flags = p->forcing;
-    fz.wind_u = p->wind_u; fz.wind_v = p->wind_v; fz.cd = p->cd;
+    fz.wind_u = p->wind_u; fz.wind_v = p->wind_v; fz.cd = p->cd; fz.cd32 = (float)p->cd;
     fz.rho0 = p->rho0 > 0 ? p->rho0 : 1025.0;
     fz.inv_rho0 = 1.0 / fz.rho0;
     fz.rho_air = p->rho_air > 0 ? p->rho_air : 1.225;

@@ -238,6 +238,27 @@ FB_HD void df_fma(float2 &s, float2 a, float2 b) {
     s.x = t;
 }
 
+// s += a * b for floats a, b: the product exact as ph + pl (the FMA gives the
+// rounding error pl), ph added by TwoSum, the low parts in float
+FB_HD void df_add_prod(float2 &s, float a, float b) {
+#ifdef __CUDA_ARCH__
+    const float ph = __fmul_rn(a, b);
+    const float pl = fmaf(a, b, -ph);
+    const float t = __fadd_rn(s.x, ph);
+    const float bb = __fsub_rn(t, s.x);
+    const float err = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fsub_rn(ph, bb));
+    s.y = __fadd_rn(s.y, __fadd_rn(err, pl));
+#else
+    const float ph = a * b;
+    const float pl = std::fmaf(a, b, -ph);
+    const float t = s.x + ph;
+    const float bb = t - s.x;
+    const float err = (s.x - (t - bb)) + (ph - bb);
+    s.y = s.y + (err + pl);
+#endif
+    s.x = t;
+}
+
 // 1/x for finite x > 0: a float estimate refined by two Newton steps on
 // f(r) = 1/r - x (r <- r + r (1 - x r)), each about doubling the correct bits
 FB_HD double rcp_nr(double x) {

@@ -14,6 +14,7 @@ struct CellArgs32 {
     float *xi_out, *xi_shadow, *hst_out, *K;
     double *h_state, *acc;      // the double time level (xi) and the correction sums
     double cdt;
+    float cdtf;                 // c tau rounded to float (float stage values)
     float fb_a, fb_b, fb_c;
 };
 
@@ -53,6 +54,7 @@ struct EdgeArgs32 {
     double *u_state, *acc;
     const float *slow;   // splitting: the slow part of Phi per edge
     double cdt;
+    float cdtf;          // c tau rounded to float (float stage values)
     float g;
     int split;           // 0, or 1: slow-term evaluation, 2: stage with Phi = fast + slow
 };
@@ -82,7 +84,8 @@ inline CellArgs32 cell_args32(const Op &op, const DevArrays &arr, const DevMesh 
     a.xiprev = f_in(arr, op.hprev);
     a.xi_out = arr.f[op.out_h]; a.xi_shadow = arr.xi32; a.hst_out = arr.f[op.hst]; a.K = arr.f[A_K];
     a.h_state = arr.a[A_H]; a.acc = arr.a[A_ACCH];
-    a.cdt = op.cdt; a.fb_a = (float)op.fb_a; a.fb_b = (float)op.fb_b; a.fb_c = (float)op.fb_c;
+    a.cdt = op.cdt; a.cdtf = (float)op.cdt;
+    a.fb_a = (float)op.fb_a; a.fb_b = (float)op.fb_b; a.fb_c = (float)op.fb_c;
     return a;
 }
 
@@ -110,7 +113,7 @@ inline EdgeArgs32 edge_args32(const Op &op, const DevArrays &arr, double g) {
     a.u0 = f_in(arr, op.u0); a.us_out = arr.f[op.out_u]; a.u_shadow = arr.u32;
     a.u_state = arr.a[A_U]; a.acc = arr.a[A_ACCU];
     a.slow = arr.f[A_SLOW];
-    a.cdt = op.cdt; a.g = (float)g;
+    a.cdt = op.cdt; a.cdtf = (float)op.cdt; a.g = (float)g;
     a.split = op.split;
     return a;
 }
@@ -137,9 +140,10 @@ inline IfArgs32 if_args32(const Op &op, const DevArrays &arr, const DevMesh &m) 
 // sum commutes) and
 // Psi_i = -(1/A_i) sum_j n_{e,i} l_e F_e (Eq. trisk_thickness).  Stage values
 // (xi_s = xi0 + c tau Psi) take the float sum.  Where the double time level
-// or a correction sum changes, the sum is taken in double from the products
-// l_e F_e (exact in double and the same from both cells), so the fluxes of an
-// edge cancel in sum_i A_i h_i to double roundoff (Theorem 1).  K_i =
+// or a correction sum changes, the sum is taken over the exact products
+// l_e F_e (the same from both cells) in double-float, about 48 bits, and
+// widened to double, so the fluxes of an edge cancel in sum_i A_i h_i far
+// below the double roundoff of the total (Theorem 1).  K_i =
 // (1/A_i) sum_j (d_e l_e / 4) u_e^2.  NMAX bounds the edges of a cell so the
 // row is loaded before the dependent gathers; the static per-edge data
 // {l_e, d_e l_e / 4, H_e} is one 16-byte gather.
@@ -156,7 +160,10 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     const float xi_i = a.xi_in[i];
     const float x0 = a.xi0[i];
     const float xp = a.fb_b != 0.f ? a.xiprev[i] : 0.f;   // the stage-2 value enters stage 3 only
-    const double invA = m.invA[i];
+    const float invAf = m.invA32[i];
+    // the double 1/A_i only where the double time level or a sum changes
+    const bool dbl = mode != SEG_UPD && mode != SEG_KONLY;
+    const double invA = dbl ? m.invA[i] : 0.0;
     if constexpr (ROWS) {
         // cell-major rows padded with valid indices: vector loads, then the
         // gathers of the first ROW_MAIN slots unconditionally (padding masked)
@@ -219,7 +226,7 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     float ke = 0.f;
     FB_UNROLL
     for (int j = 0; j < NMAX; ++j) ke += kw[j] * ue[j] * ue[j];
-    a.K[i] = ke * (float)invA;
+    a.K[i] = ke * invAf;
     if (mode == SEG_KONLY) return;
     float F[NMAX];
     FB_UNROLL
@@ -229,15 +236,19 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
         float S = 0.f;
         FB_UNROLL
         for (int j = 0; j < NMAX; ++j) S += sdv[j] * F[j];
-        const float xs = x0 + (float)a.cdt * (S * (float)invA);
+        const float xs = x0 + a.cdtf * (S * invAf);
         a.xi_out[i] = xs;
         a.hst_out[i] = a.fb_a * xs + a.fb_b * xp + a.fb_c * x0;
         if (mode == SEG_UPD) return;
     }
-    double S = 0.0;
+    // the products l_e F_e are exact as float pairs (Dekker's product through
+    // an FMA) and are summed in double-float on the FP32 pipe (Knuth's
+    // TwoSum), then widened once: the edge's two cells take the same exact
+    // product, and GB300 spends no FP64 operation per slot
+    float2 Sd = make_float2(0.f, 0.f);
     FB_UNROLL
-    for (int j = 0; j < NMAX; ++j) S = fma((double)sdv[j], (double)F[j], S);
-    const double psi = S * invA;
+    for (int j = 0; j < NMAX; ++j) df_add_prod(Sd, sdv[j], F[j]);
+    const double psi = df_value(Sd) * invA;
     switch (mode) {
         case SEG_INPLACE: {
             const double hn = a.h_state[i] + a.cdt * psi;
@@ -386,7 +397,7 @@ FB_HD float phi_from_shares(const DevMesh &m, const float *u_in, const DevForcin
             const float dn = w.x - ue, dt = w.y - vt;
             phi += w.z * sqrtf(dn * dn + dt * dt) * dn * rhe;
         }
-        if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue * rhe;
+        if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= fz.cd32 * sqrtf(ue * ue + vt * vt) * ue * rhe;
     }
     return phi;
 }
@@ -396,23 +407,24 @@ FB_HD float phi_from_shares(const DevMesh &m, const float *u_in, const DevForcin
 // No-flow edges take u = 0 and contribute 0.
 template <class A>
 FB_HD void edge32_apply(const A &a, int mode, int e, bool bnd, float phi) {
+    const double phid = df_widen(phi);   // exact, on the integer pipe (no FP64 conversion)
     switch (mode) {
-        case SEG_UPD: a.us_out[e] = bnd ? 0.f : a.u0[e] + (float)a.cdt * phi; break;
+        case SEG_UPD: a.us_out[e] = bnd ? 0.f : a.u0[e] + a.cdtf * phi; break;
         case SEG_INPLACE: {
-            const double un = bnd ? 0.0 : a.u_state[e] + a.cdt * (double)phi;
+            const double un = bnd ? 0.0 : a.u_state[e] + a.cdt * phid;
             a.u_state[e] = un;
             a.u_shadow[e] = (float)un;
         } break;
-        case SEG_ACC_SET: a.acc[e] = (double)phi; break;
-        case SEG_ACC_ADD: a.acc[e] += (double)phi; break;
+        case SEG_ACC_SET: a.acc[e] = phid; break;
+        case SEG_ACC_ADD: a.acc[e] += phid; break;
         case SEG_PHI: a.us_out[e] = bnd ? 0.f : phi; break;
         case SEG_RK_SET:
         case SEG_RK_ADD2:
-            a.us_out[e] = bnd ? 0.f : a.u0[e] + (float)a.cdt * phi;
-            a.acc[e] = mode == SEG_RK_SET ? (double)phi : a.acc[e] + 2.0 * (double)phi;
+            a.us_out[e] = bnd ? 0.f : a.u0[e] + a.cdtf * phi;
+            a.acc[e] = mode == SEG_RK_SET ? phid : a.acc[e] + 2.0 * phid;
             break;
         case SEG_RK_FIN: {
-            const double un = bnd ? 0.0 : a.u_state[e] + a.cdt * (a.acc[e] + (double)phi);
+            const double un = bnd ? 0.0 : a.u_state[e] + a.cdt * (a.acc[e] + phid);
             a.u_state[e] = un;
             a.u_shadow[e] = (float)un;
         } break;
@@ -463,7 +475,7 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
                     const float dn = w.x - ue, dt = w.y - vt;
                     phi += w.z * sqrtf(dn * dn + dt * dt) * dn / he;
                 }
-                if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= (float)fz.cd * sqrtf(ue * ue + vt * vt) * ue / he;
+                if (fz.flags & FBLTS_FORCE_BOTTOM_DRAG) phi -= fz.cd32 * sqrtf(ue * ue + vt * vt) * ue / he;
                 if (fz.flags & FBLTS_FORCE_VORTEX) phi -= (fz.ps32[c1] - fz.ps32[c0]) * idc / (float)fz.rho0;
             }
         }

@@ -35,6 +35,7 @@ struct DevMesh {
     const float4 *vCf;
     const float4 *vKh;
     const double *invA;                 // 1 / A_i
+    const float *invA32;                // 1 / A_i rounded to float (FP32 stage values and K)
     // neighbour edges from the cells' edge rows (FP32 edge pass): rowS = 8 or
     // 12 when valid, else 0 (explicit lists eoe / woe32, woe32 = W / l_{e'})
     int rowS;
@@ -59,6 +60,7 @@ struct DevForcing {
     float4 *wrec32;
     float *ps32;
     double wind_u, wind_v, cd, rho0, rho_air;
+    float cd32;                // cd rounded to float (FP32 edge pass)
     double inv_rho0;           // 1 / rho0 (the per-edge pressure force multiplies by it)
     double vx[9];
     double t0, dt;
