@@ -423,8 +423,8 @@ static std::vector<size_t> state_plan(const fblts_mesh *m, bool f32) {
     };
     auto count = [&](int a) -> size_t {
         // FP32 path: the edge records {l F, q_e, l u, 0}, or with cell rows the
-        // two cells' 16-byte shares per edge
-        if (a == A_FQU) return (m->dm.rowS ? 8 : 4) * nE;
+        // two cells' 8-byte shares per edge and a {B, xi*} record per cell
+        if (a == A_FQU) return m->dm.rowS ? 4 * nE + 2 * nC : 4 * nE;
         return arr_is_cell(a) ? nC : (arr_is_vert(a) ? nV : nE);
     };
     const size_t szc = sizeof(double) * nC, sze = sizeof(double) * nE;
@@ -437,6 +437,7 @@ static std::vector<size_t> state_plan(const fblts_mesh *m, bool f32) {
         plan.push_back(4 * nC); plan.push_back(4 * nE);            // shadows
         plan.push_back(4 * nE);                                    // H_e
         plan.push_back(16 * nE);                                   // per-edge record
+        plan.push_back(8 * nE);                                    // per-edge {l_e, H_e} (TRiSK pass)
         plan.push_back(16 * nV);                                   // per-vertex record
         plan.push_back(16 * nE); plan.push_back(4 * nC);           // forcing (float): per-edge record, p_s
     }
@@ -569,6 +570,8 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         s->arr.a[a] = is_double(a) ? (double *)ptr : nullptr;
         s->arr.f[a] = is_double(a) ? nullptr : (float *)ptr;
     }
+    // the TRiSK pass's per-cell records follow its per-edge shares (4 floats per edge)
+    s->arr.bx32 = (f32 && m->dm.rowS) ? s->arr.f[A_FQU] + 4 * (size_t)m->hm.nE : nullptr;
     double *db = (double *)got[gi++];
     s->fz.windN = (double *)got[gi++];
     s->fz.windT = (double *)got[gi++];
@@ -581,11 +584,13 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     }
     float *He32 = nullptr;
     float4 *estat = nullptr, *vkh = nullptr;
+    float2 *el2 = nullptr;
     if (f32) {
         s->arr.xi32 = (float *)got[gi++];
         s->arr.u32 = (float *)got[gi++];
         He32 = (float *)got[gi++];
         estat = (float4 *)got[gi++];
+        el2 = (float2 *)got[gi++];
         vkh = (float4 *)got[gi++];
         s->fz.wrec32 = (float4 *)got[gi++];
         s->fz.ps32 = (float *)got[gi++];
@@ -619,8 +624,8 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     }
     if (st == FBLTS_OK) st = upload_state(s, h0, u0);
     if (st == FBLTS_OK && f32) {
-        s->dm.He32 = He32; s->dm.estat = estat; s->dm.vKh = vkh;
-        if (launch_fp32_depths(s->dm, He32, estat, vkh, s->st) != cudaSuccess ||
+        s->dm.He32 = He32; s->dm.estat = estat; s->dm.el2 = el2; s->dm.vKh = vkh;
+        if (launch_fp32_depths(s->dm, He32, estat, el2, vkh, s->st) != cudaSuccess ||
             launch_fp32_shadows(s->dm, s->arr, s->st) != cudaSuccess) {
             set_error("state_init: FP32 setup failed");
             st = FBLTS_E_CUDA;

@@ -196,6 +196,22 @@ FB_HD float df_trunc(double x) {
     return fb_ffrom_bits(sign | ((unsigned)e << 23) | m);
 }
 
+// x rounded to the nearest float, ties to even (the IEEE conversion), on the
+// integer pipe for results in the normal float range; the rare results
+// below it (|x| < 2^-126, zero included) take the conversion instruction
+FB_HD float df_round(double x) {
+    const unsigned long long b = fb_bits(x);
+    const int ed = (int)((b >> 52) & 0x7FFu);
+    const int e = ed - 1023 + 127;
+    if (e <= 0 || ed == 0x7FF) return (float)x;
+    if (e >= 255) return fb_ffrom_bits((unsigned)(b >> 32) & 0x80000000u ? 0xFF800000u : 0x7F800000u);
+    const unsigned long long mant = b & ((1ull << 52) - 1ull);
+    unsigned r = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) | (unsigned)(mant >> 29);
+    const unsigned rem = (unsigned)(mant & ((1ull << 29) - 1ull));
+    if (rem > (1u << 28) || (rem == (1u << 28) && (r & 1u))) ++r;   // a carry moves into the exponent (to infinity past the largest float)
+    return fb_ffrom_bits(r);
+}
+
 // the double value of a float (exact; subnormal floats become 0)
 FB_HD double df_widen(float f) {
     const unsigned u = fb_fbits(f);

@@ -34,13 +34,14 @@ struct PrepArgs32 {
 // meshes); longer rows take a branch for the rest
 constexpr int ROW_MAIN = 6;
 
-// Cell-side TRiSK pass: per slot of each cell, the share {t, s_v, B_i, xi*_i}
-// of the cell in its edge's momentum tendency (trisk32_body), written to
-// half[2 e + side] (side 0 = first cell of e).
+// Cell-side TRiSK pass: per slot of each cell, the share {t, s_v} of the
+// cell in its edge's momentum tendency (trisk32_body), written to
+// sh[2 e + side] (side 0 = first cell of e), and per cell {B_i, xi*_i} to
+// bx[i]; both live in the A_FQU area (shares first, 4 floats per edge).
 struct TriskArgs32 {
     int lo, hi;
     const float *u_in, *hst, *K, *q;
-    float4 *half;
+    float2 *sh, *bx;
     float g, inv_rho0;
 };
 
@@ -49,7 +50,7 @@ struct EdgeArgs32 {
     int lo, hi;
     const float *u_in, *hst, *K, *u0;
     const float4 *fqu;
-    const float4 *half;
+    const float2 *sh, *bx;   // the TRiSK pass's shares and per-cell {B, xi*}
     float *us_out, *u_shadow;
     double *u_state, *acc;
     const float *slow;   // splitting: the slow part of Phi per edge
@@ -100,7 +101,8 @@ inline PrepArgs32 prep_args32(const Op &op, const DevArrays &arr) {
 inline TriskArgs32 trisk_args32(const Op &op, const DevArrays &arr, double g, double rho0) {
     // the slow-term evaluation of the splitting leaves the gravity term out of B
     return TriskArgs32{op.lo, op.hi, f_in(arr, op.in_u), f_in(arr, op.hst), arr.f[A_K], arr.f[A_Q],
-                       (float4 *)arr.f[A_FQU], op.split == 1 ? 0.f : (float)g,
+                       (float2 *)arr.f[A_FQU], (float2 *)arr.bx32,
+                       op.split == 1 ? 0.f : (float)g,
                        (float)(rho0 > 0.0 ? 1.0 / rho0 : 0.0)};
 }
 
@@ -109,7 +111,8 @@ inline EdgeArgs32 edge_args32(const Op &op, const DevArrays &arr, double g) {
     a.segs = segs_of(op);
     a.lo = op.lo; a.hi = op.hi;
     a.u_in = f_in(arr, op.in_u); a.hst = f_in(arr, op.hst); a.K = arr.f[A_K]; a.fqu = (const float4 *)arr.f[A_FQU];
-    a.half = (const float4 *)arr.f[A_FQU];
+    a.sh = (const float2 *)arr.f[A_FQU];
+    a.bx = (const float2 *)arr.bx32;
     a.u0 = f_in(arr, op.u0); a.us_out = arr.f[op.out_u]; a.u_shadow = arr.u32;
     a.u_state = arr.a[A_U]; a.acc = arr.a[A_ACCU];
     a.slow = arr.f[A_SLOW];
@@ -252,7 +255,7 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     switch (mode) {
         case SEG_INPLACE: {
             const double hn = a.h_state[i] + a.cdt * psi;
-            const float xs = (float)hn;
+            const float xs = df_round(hn);
             a.h_state[i] = hn;
             a.xi_shadow[i] = xs;
             a.hst_out[i] = a.fb_a * xs + a.fb_b * xp + a.fb_c * x0;
@@ -263,7 +266,7 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
         case SEG_RK_ADD2: a.acc[i] += 2.0 * psi; break;
         case SEG_RK_FIN: {
             const double hn = a.h_state[i] + a.cdt * (a.acc[i] + psi);
-            const float xs = (float)hn;
+            const float xs = df_round(hn);
             a.h_state[i] = hn;
             a.xi_shadow[i] = xs;
             a.hst_out[i] = a.fb_a * xs + a.fb_b * xp + a.fb_c * x0;
@@ -304,10 +307,10 @@ FB_HD void prep32_body(const DevMesh &m, const PrepArgs32 &a, int e) {
 //   sum_j W_kj d X_j / l_j = n_k (1/2 (T - y_k) - T_P + P_k T - C_k),
 // T = sum_j y_j, T_P = sum_j P_j y_j, C_k = sum_{j<k} y_j: O(n) per cell.
 // X = l F (F = h_e u from the FB-averaged thickness) gives s0, X = l F q_e
-// gives s1, X = l u gives s_v.  The share of slot k is
-//   {t = q_{e_k} s0 + s1, s_v, B_i = K_i + g xi*_i (+ p_s / rho0), xi*_i},
+// gives s1, X = l u gives s_v.  The share of slot k is {t = q_{e_k} s0 + s1,
+// s_v} and the cell writes {B_i = K_i + g xi*_i (+ p_s / rho0), xi*_i} once,
 // so the edge pass forms Phi_e = [(t_0 + t_1)/2 - (B_c1 - B_c0)] / d_e from
-// two coalesced loads.  q_{e_k} = (q at the two vertices of e_k) / 2: the
+// one coalesced 16-byte load and the two cells' records.  q_{e_k} = (q at the two vertices of e_k) / 2: the
 // row's vertex k is the counter-clockwise end of e_k, vertex k-1 the other.
 // Rows are padded to S slots with valid indices; slots >= nEoC are masked.
 template <int S, bool VORTEX>
@@ -343,12 +346,12 @@ FB_HD void trisk32_body(const DevMesh &m, const TriskArgs32 &a, const DevForcing
         qv[j] = 0.f;
         if (j < ROW_MAIN || n > ROW_MAIN) {
             const int e = re[j] < 0 ? ~re[j] : re[j];
-            const float4 st = m.estat[e];
+            const float2 st = m.el2[e];   // {l_e, H_e}
             const float u = a.u_in[e];
             const float xn = a.hst[rn[j]];
             qv[j] = a.q[rv[j]];
             lu[j] = j < n ? st.x * u : 0.f;
-            lF[j] = (st.z + 0.5f * (xs + xn)) * lu[j];
+            lF[j] = (st.y + 0.5f * (xs + xn)) * lu[j];
         }
     }
     float qlast = qv[0];
@@ -374,25 +377,28 @@ FB_HD void trisk32_body(const DevMesh &m, const TriskArgs32 &a, const DevForcing
             const float s1 = sg * (0.5f * (T1 - y1) - P1 + P[k] * T1 - C1);
             const float sv = sg * (0.5f * (Tv - yv) - Pv + P[k] * Tv - Cv);
             const int e = re[k] < 0 ? ~re[k] : re[k];
-            a.half[2 * e + (re[k] < 0 ? 1 : 0)] = make_float4(qe[k] * s0 + s1, sv, B, xs);
+            a.sh[2 * e + (re[k] < 0 ? 1 : 0)] = make_float2(qe[k] * s0 + s1, sv);
         }
         C0 += y0; C1 += y1; Cv += yv;
     }
+    a.bx[i] = make_float2(B, xs);   // last: a store before the gathers would hold them back
 }
 
-// Phi_e from the two cells' shares {t, s_v, B, xi*} (trisk32_shares):
-// Phi_e = [(t_0 + t_1)/2 - (B_1 - B_0)] / d_e plus, with forcing, the wind
-// stress and quadratic drag (Eq. hurricane_model) with v_e = (s_v0 + s_v1) / d_e
-// and h_e = H_e + (xi*_0 + xi*_1)/2; the surface pressure is inside B.
+// Phi_e from the two cells' shares {t, s_v} and records {B, xi*}
+// (trisk32_body): Phi_e = [(t_0 + t_1)/2 - (B_1 - B_0)] / d_e plus, with
+// forcing, the wind stress and quadratic drag (Eq. hurricane_model) with
+// v_e = (s_v0 + s_v1) / d_e and h_e = H_e + (xi*_0 + xi*_1)/2; the surface
+// pressure is inside B.
 template <bool FORCING>
-FB_HD float phi_from_shares(const DevMesh &m, const float *u_in, const DevForcing &fz, int e, float4 h0, float4 h1) {
+FB_HD float phi_from_shares(const DevMesh &m, const float *u_in, const DevForcing &fz, int e, float4 s, float2 b0,
+                            float2 b1) {
     const float idc = m.invDc32[e];
-    float phi = idc * (0.5f * (h0.x + h1.x) - (h1.z - h0.z));
+    float phi = idc * (0.5f * (s.x + s.z) - (b1.x - b0.x));
     if (FORCING) {
-        const float vt = idc * (h0.y + h1.y);
+        const float vt = idc * (s.y + s.w);
         const float ue = u_in[e];
         const float4 w = fz.wrec32[e];   // {wind normal, wind tangential, C_W, H_e}
-        const float rhe = 1.f / (w.w + 0.5f * (h0.w + h1.w));
+        const float rhe = 1.f / (w.w + 0.5f * (b0.y + b1.y));
         if (fz.flags & FBLTS_FORCE_WIND_STRESS) {
             const float dn = w.x - ue, dt = w.y - vt;
             phi += w.z * sqrtf(dn * dn + dt * dt) * dn * rhe;
@@ -413,7 +419,7 @@ FB_HD void edge32_apply(const A &a, int mode, int e, bool bnd, float phi) {
         case SEG_INPLACE: {
             const double un = bnd ? 0.0 : a.u_state[e] + a.cdt * phid;
             a.u_state[e] = un;
-            a.u_shadow[e] = (float)un;
+            a.u_shadow[e] = df_round(un);
         } break;
         case SEG_ACC_SET: a.acc[e] = phid; break;
         case SEG_ACC_ADD: a.acc[e] += phid; break;
@@ -426,7 +432,7 @@ FB_HD void edge32_apply(const A &a, int mode, int e, bool bnd, float phi) {
         case SEG_RK_FIN: {
             const double un = bnd ? 0.0 : a.u_state[e] + a.cdt * (a.acc[e] + phid);
             a.u_state[e] = un;
-            a.u_shadow[e] = (float)un;
+            a.u_shadow[e] = df_round(un);
         } break;
         default: break;
     }
@@ -449,7 +455,8 @@ FB_HD void edge32_body(const DevMesh &m, const EdgeArgs32 &a, const DevForcing &
         phi = a.slow[e] - a.g * (a.hst[m.coe1[e]] - a.hst[m.coe0[e]]) * m.invDc32[e];
     } else if (!bnd) {
         if constexpr (SHARES) {
-            phi = phi_from_shares<FORCING>(m, a.u_in, fz, e, a.half[2 * e], a.half[2 * e + 1]);
+            const float4 s = *reinterpret_cast<const float4 *>(a.sh + 2 * (size_t)e);   // {t0, s_v0, t1, s_v1}
+            phi = phi_from_shares<FORCING>(m, a.u_in, fz, e, s, a.bx[m.coe0[e]], a.bx[m.coe1[e]]);
         } else {
             // explicit neighbour list; the weights are W_{e,e'} / l_{e'}
             const float idc = m.invDc32[e];
@@ -504,7 +511,7 @@ FB_HD void pred32_body(const IfArgs32 &a, int t) {
     const float wk = a.k / Md, wk1 = (a.k + 1) / Md, w1 = 1.f / Md;
     const int i = a.c_lo + t;
     if (i < a.c_if1_hi) {
-        const float x0 = (float)a.sh0[i];
+        const float x0 = df_round(a.sh0[i]);
         const float x13 = a.sh1[i], x12 = a.sh2[i], x1 = a.sh3[i];
         const float hk = wk * x1 + (1.f - wk) * x0;
         const float hk1 = wk1 * x1 + (1.f - wk1) * x0;
@@ -519,7 +526,7 @@ FB_HD void pred32_body(const IfArgs32 &a, int t) {
     }
     const int e = a.e_lo + t;
     if (e < a.e_if1_hi) {
-        const float x0 = (float)a.su0[e], x13 = a.su1[e], x12 = a.su2[e], x1 = a.su3[e];
+        const float x0 = df_round(a.su0[e]), x13 = a.su1[e], x12 = a.su2[e], x1 = a.su3[e];
         a.u32[e] = wk * x1 + (1.f - wk) * x0;
         a.us1[e] = wk * x1 + w1 * x13 + (1.f - wk1) * x0;
         a.us2[e] = wk * x1 + w1 * x12 + (1.f - wk1) * x0;
@@ -532,13 +539,13 @@ FB_HD void final32_body(const IfArgs32 &a, const unsigned char *ebnd, int t) {
     if (i < a.c_if12_hi) {
         const double hn = a.sh0[i] + a.cf * a.acch[i];
         a.h[i] = hn;
-        a.xi[i] = (float)hn;
+        a.xi[i] = df_round(hn);
     }
     const int e = a.e_lo + t;
     if (e < a.e_if12_hi) {
         const double un = ebnd[e] ? 0.0 : a.su0[e] + a.cf * a.accu[e];
         a.u[e] = un;
-        a.u32[e] = (float)un;
+        a.u32[e] = df_round(un);
     }
 }
 

@@ -478,14 +478,14 @@ static double op_bytes(const HostMesh &hm, Toucher &tch, const Op &op, int forci
             const std::vector<std::pair<int, int>> r = {{op.lo, op.hi}};
             const Touched &t = tch.get(OP_TRISK, r);
             // cells: nEoC, K, rows {signed edge, kite prefix, neighbour cell,
-            // vertex} (moved: at their stored width, and one 16-byte share out
+            // vertex} (moved: at their stored width, and one 8-byte share out
             // per slot), (vortex) p_s | edges: u_in, l_e and H_e (moved: the
-            // record {l, d l / 4, H_e}) | hst at the cells and their neighbours
+            // record {l_e, H_e}) | hst at the cells and their neighbours
             // | q at the vertices
             const double rows = alg ? t.slots * 16 : t.self * hm.rowS * 16;
-            b = t.self * (4 + R + (vortex ? R : 0)) + rows + t.edges * (R + (alg ? 2 * C : 16)) + t.cells * R +
+            b = t.self * (4 + R + (vortex ? R : 0)) + rows + t.edges * (R + (alg ? 2 * C : 8)) + t.cells * R +
                 t.verts * R;
-            if (!alg) b += t.slots * 16;
+            if (!alg) b += t.slots * 8 + t.self * 8;   // shares {t, s_v}, the cell's {B, xi*}
         } break;
         case OP_EDGE: {
             if (all.empty()) break;
@@ -499,12 +499,14 @@ static double op_bytes(const HostMesh &hm, Toucher &tch, const Op &op, int forci
                 break;
             }
             if (fp32 && hm.rows_canonical) {
-                // ebnd, 1/d_e (moved: the two cells' 16-byte shares)
+                // ebnd, 1/d_e (moved: the two cells' 8-byte shares, coe and the
+                // cells' {B, xi*} records)
                 for (int k = 0; k < op.nseg; ++k) {
                     const double n = op.seg[k].end - op.seg[k].begin;
-                    b += n * (1 + 4 + (alg ? 0 : 32)) + per_mode(n, op.seg[k].mode, false);
+                    b += n * (1 + 4 + (alg ? 0 : 16 + 8)) + per_mode(n, op.seg[k].mode, false);
                     if (forcing) b += n * (R + 4 + 3 * R);   // u_in, H_e, wind, C_W
                 }
+                if (!alg) b += tch.get(OP_EPREP, all).cells * 8;
                 break;
             }
             const Touched &t = tch.get(OP_EDGE, all);
