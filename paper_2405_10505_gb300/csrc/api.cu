@@ -436,8 +436,7 @@ static std::vector<size_t> state_plan(const fblts_mesh *m, bool f32) {
     if (f32) {
         plan.push_back(4 * nC); plan.push_back(4 * nE);            // shadows
         plan.push_back(4 * nE);                                    // H_e
-        plan.push_back(16 * nE);                                   // per-edge record
-        plan.push_back(8 * nE);                                    // per-edge {l_e, H_e} (TRiSK pass)
+        plan.push_back(8 * nE);                                    // per-edge record {l_e, H_e}
         plan.push_back(16 * nV);                                   // per-vertex record
         plan.push_back(16 * nE); plan.push_back(4 * nC);           // forcing (float): per-edge record, p_s
     }
@@ -583,13 +582,12 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
         Hv64 = (double *)got[gi++];
     }
     float *He32 = nullptr;
-    float4 *estat = nullptr, *vkh = nullptr;
+    float4 *vkh = nullptr;
     float2 *el2 = nullptr;
     if (f32) {
         s->arr.xi32 = (float *)got[gi++];
         s->arr.u32 = (float *)got[gi++];
         He32 = (float *)got[gi++];
-        estat = (float4 *)got[gi++];
         el2 = (float2 *)got[gi++];
         vkh = (float4 *)got[gi++];
         s->fz.wrec32 = (float4 *)got[gi++];
@@ -624,8 +622,8 @@ extern "C" fblts_status fblts_state_init(const fblts_mesh *m, const fblts_params
     }
     if (st == FBLTS_OK) st = upload_state(s, h0, u0);
     if (st == FBLTS_OK && f32) {
-        s->dm.He32 = He32; s->dm.estat = estat; s->dm.el2 = el2; s->dm.vKh = vkh;
-        if (launch_fp32_depths(s->dm, He32, estat, el2, vkh, s->st) != cudaSuccess ||
+        s->dm.He32 = He32; s->dm.el2 = el2; s->dm.vKh = vkh;
+        if (launch_fp32_depths(s->dm, He32, el2, vkh, s->st) != cudaSuccess ||
             launch_fp32_shadows(s->dm, s->arr, s->st) != cudaSuccess) {
             set_error("state_init: FP32 setup failed");
             st = FBLTS_E_CUDA;

@@ -148,8 +148,8 @@ inline IfArgs32 if_args32(const Op &op, const DevArrays &arr, const DevMesh &m) 
 // widened to double, so the fluxes of an edge cancel in sum_i A_i h_i far
 // below the double roundoff of the total (Theorem 1).  K_i =
 // (1/A_i) sum_j (d_e l_e / 4) u_e^2.  NMAX bounds the edges of a cell so the
-// row is loaded before the dependent gathers; the static per-edge data
-// {l_e, d_e l_e / 4, H_e} is one 16-byte gather.
+// row is loaded before the dependent gathers; the static per-edge data are
+// an 8-byte {l_e, H_e} and a 4-byte d_e l_e / 4 gather.
 template <int NMAX, bool ROWS>
 FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
     const int mode = seg_mode(a.segs, i);
@@ -189,11 +189,12 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
             if (j < ROW_MAIN || n > ROW_MAIN) {   // slots past ROW_MAIN only for cells that have them
                 const int e = er[j] < 0 ? ~er[j] : er[j];
                 const float u = a.u_in[e];
-                const float4 st = m.estat[e];
+                const float2 st = m.el2[e];   // {l_e, H_e}
+                const float kwe = m.ke32[e];  // d_e l_e / 4
                 xn[j] = a.xi_in[nb[j]];
                 ue[j] = j < n ? u : 0.f;
-                kw[j] = st.y;
-                He[j] = st.z;
+                kw[j] = kwe;
+                He[j] = st.y;
                 sdv[j] = j < n ? (er[j] < 0 ? st.x : -st.x) : 0.f;    // -n_{e,i} l_e
             }
         }
@@ -219,9 +220,9 @@ FB_HD void cell32_body(const DevMesh &m, const CellArgs32 &a, int i) {
                 const int e = er[j] < 0 ? ~er[j] : er[j];
                 ue[j] = a.u_in[e];
                 xn[j] = a.xi_in[nb[j]];
-                const float4 st = m.estat[e];
-                kw[j] = st.y;
-                He[j] = st.z;
+                const float2 st = m.el2[e];   // {l_e, H_e}
+                kw[j] = m.ke32[e];            // d_e l_e / 4
+                He[j] = st.y;
                 sdv[j] = er[j] < 0 ? st.x : -st.x;    // -n_{e,i} l_e
             }
         }

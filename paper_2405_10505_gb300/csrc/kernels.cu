@@ -133,15 +133,13 @@ __global__ void __launch_bounds__(TPB) forcing32_pass(DevMesh m, DevForcing fz) 
 }
 
 // resting depth seen by the FP32 path: H_e, the mean over the two cells of an
-// edge (also in the per-edge records {l_e, d_e l_e / 4, H_e, 0} and
-// {l_e, H_e}), and the per-vertex record {kite / A_v x3, H_v} with the
-// kite-weighted mean H_v
-__global__ void fp32_depths(DevMesh m, float *He32, float4 *estat, float2 *el2, float4 *vkh) {
+// edge (also in the per-edge record {l_e, H_e}), and the per-vertex record
+// {kite / A_v x3, H_v} with the kite-weighted mean H_v
+__global__ void fp32_depths(DevMesh m, float *He32, float2 *el2, float4 *vkh) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < m.nE) {
         const float He = (float)(-0.5 * (m.bottom[m.coe0[t]] + m.bottom[m.coe1[t]]));
         He32[t] = He;
-        estat[t] = make_float4(m.dv32[t], m.ke32[t], He, 0.f);
         el2[t] = make_float2(m.dv32[t], He);
     }
     if (t < m.nV) {
@@ -340,10 +338,10 @@ static cudaError_t launch_op32(const Op &op, const DevMesh &m, const DevArrays &
     return cudaGetLastError();
 }
 
-cudaError_t launch_fp32_depths(const DevMesh &m, float *He32, float4 *estat, float2 *el2,
+cudaError_t launch_fp32_depths(const DevMesh &m, float *He32, float2 *el2,
                                float4 *vkh, cudaStream_t st) {
     const int n = m.nE > m.nV ? (m.nE > m.nC ? m.nE : m.nC) : (m.nV > m.nC ? m.nV : m.nC);
-    fp32_depths<<<nblk(n), TPB, 0, st>>>(m, He32, estat, el2, vkh);
+    fp32_depths<<<nblk(n), TPB, 0, st>>>(m, He32, el2, vkh);
     return cudaGetLastError();
 }
 

@@ -27,8 +27,7 @@ struct DevMesh {
     // neighbour edges from the cells' edge rows: slots and weights in row order (FP32 path)
     const int *eocS;                    // edge rows with the sign n_{e,i} (~e for the second cell)
     const float *dv32, *ke32;           // l_e and d_e l_e / 4 per edge
-    const float4 *estat;                // per edge {l_e, d_e l_e / 4, H_e, 0} (H_e per state)
-    const float2 *el2;                  // per edge {l_e, H_e} (per state; the TRiSK pass)
+    const float2 *el2;                  // per edge {l_e, H_e} (H_e per state)
     // FP32 vertex pass, one record per vertex: {eov x3, cov[0]}, {cov[1], cov[2]},
     // {t_{e,v} d_e / A_v x3, f_v}, and per state {kite / A_v x3, H_v}
     const int4 *vI4;
@@ -96,7 +95,7 @@ cudaError_t launch_op(const Op &op, const DevMesh &m, const DevArrays &arr, cons
 
 // FP32-tendency path: resting depths seen by the float kernels, and the
 // float shadows of the double time level (after any write of h, u)
-cudaError_t launch_fp32_depths(const DevMesh &m, float *He32, float4 *estat, float2 *el2,
+cudaError_t launch_fp32_depths(const DevMesh &m, float *He32, float2 *el2,
                                float4 *vkh, cudaStream_t st);
 cudaError_t launch_fp32_shadows(const DevMesh &m, const DevArrays &arr, cudaStream_t st);
 

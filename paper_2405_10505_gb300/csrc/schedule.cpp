@@ -447,13 +447,19 @@ static double op_bytes(const HostMesh &hm, Toucher &tch, const Op &op, int forci
             if (all.empty()) break;
             // cells: nEoC, K out, (alg, or fp32) 1/A; rows (signed edge,
             // neighbour cell); edges: u_in and the metrics l_e, d_e l_e / 4
-            // (fp32: one record with H_e; fp64 moved: per-slot coefficients
-            // with 1/A folded in); xi / h at the cells
+            // (fp32: {l_e, H_e} and d_e l_e / 4; fp64 moved: per-slot
+            // coefficients with 1/A folded in); xi / h at the cells.  FP32
+            // reads 1/A as a float, and as a double too where the double
+            // time level or a correction sum changes
             bool konly = true;
-            for (int k = 0; k < op.nseg; ++k) konly = konly && op.seg[k].mode == SEG_KONLY;
+            double ndbl = 0;
+            for (int k = 0; k < op.nseg; ++k) {
+                konly = konly && op.seg[k].mode == SEG_KONLY;
+                if (op.seg[k].mode != SEG_KONLY && op.seg[k].mode != SEG_UPD) ndbl += op.seg[k].end - op.seg[k].begin;
+            }
             const Touched &t = tch.get(OP_CELL, all);
             b += t.self * (4 + R) + t.slots * 4 + t.edges * R;
-            if (fp32) b += t.self * 8 + t.edges * REC;
+            if (fp32) b += t.self * 4 + ndbl * 8 + t.edges * 12;
             else if (alg) b += t.self * 8 + t.edges * 2 * C;
             else b += t.slots * C;                                  // cKE per slot
             if (!konly) b += t.slots * (4 + (fp32 || alg ? 0 : C)) + t.cells * R;   // coc (+ cDiv), h_in
