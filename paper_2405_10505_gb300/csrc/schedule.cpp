@@ -458,11 +458,16 @@ static double op_bytes(const HostMesh &hm, Toucher &tch, const Op &op, int forci
                 if (op.seg[k].mode != SEG_KONLY && op.seg[k].mode != SEG_UPD) ndbl += op.seg[k].end - op.seg[k].begin;
             }
             const Touched &t = tch.get(OP_CELL, all);
-            b += t.self * (4 + R) + t.slots * 4 + t.edges * R;
+            // moved, FP32 with cell rows: both rows at their stored width and
+            // the neighbour thickness gathered in every launch (the kernel
+            // issues all its loads in one round, K-only cells included)
+            const bool rows = !alg && fp32 && hm.rows_canonical;
+            b += t.self * (4 + R) + (rows ? t.self * hm.rowS * 8 : t.slots * 4) + t.edges * R;
             if (fp32) b += t.self * 4 + ndbl * 8 + t.edges * 12;
             else if (alg) b += t.self * 8 + t.edges * 2 * C;
             else b += t.slots * C;                                  // cKE per slot
-            if (!konly) b += t.slots * (4 + (fp32 || alg ? 0 : C)) + t.cells * R;   // coc (+ cDiv), h_in
+            if (rows) b += t.cells * R;
+            else if (!konly) b += t.slots * (4 + (fp32 || alg ? 0 : C)) + t.cells * R;   // coc (+ cDiv), h_in
             if (!konly && !fp32) b += t.edges * 8;                  // H_e
             for (int k = 0; k < op.nseg; ++k)
                 b += per_mode(op.seg[k].end - op.seg[k].begin, op.seg[k].mode, true);
