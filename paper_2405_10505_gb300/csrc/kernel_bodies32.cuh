@@ -144,9 +144,9 @@ inline IfArgs32 if_args32(const Op &op, const DevArrays &arr, const DevMesh &m) 
 // Psi_i = -(1/A_i) sum_j n_{e,i} l_e F_e (Eq. trisk_thickness).  Stage values
 // (xi_s = xi0 + c tau Psi) take the float sum.  Where the double time level
 // or a correction sum changes, the sum is taken over the exact products
-// l_e F_e (the same from both cells) in double-float, about 48 bits, and
-// widened to double, so the fluxes of an edge cancel in sum_i A_i h_i far
-// below the double roundoff of the total (Theorem 1).  K_i =
+// l_e F_e (the same from both cells) in double-float, within 2^-44 of the
+// largest product, and widened to double, so the fluxes of an edge cancel in
+// sum_i A_i h_i far below the double roundoff of the total (Theorem 1).  K_i =
 // (1/A_i) sum_j (d_e l_e / 4) u_e^2.  NMAX bounds the edges of a cell so the
 // row is loaded before the dependent gathers; the static per-edge data are
 // an 8-byte {l_e, H_e} and a 4-byte d_e l_e / 4 gather.
