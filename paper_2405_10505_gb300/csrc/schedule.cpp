@@ -426,7 +426,9 @@ static double op_bytes(const HostMesh &hm, Toucher &tch, const Op &op, int forci
         if (mode == SEG_UPD)   // stage inputs at the element, stage output (+ FB average for cells)
             x = cell ? n * R * (3 + (op.stage == 3 ? 1 : 0)) : n * 2 * R;
         if (mode == SEG_INPLACE) {
-            if (cell) x = fp32 ? n * (16 + 8 + 4 + 4 + 4 + (op.stage == 3 ? 4 : 0)) : n * (16 + 8 + 8);
+            // FP32 cells: the double time level read and written, its float
+            // shadow, xi0 and the FB average out (+ the stage-2 xi in stage 3)
+            if (cell) x = fp32 ? n * (16 + 4 + 4 + 4 + (op.stage == 3 ? 4 : 0)) : n * (16 + 8 + 8);
             else x = fp32 ? n * (16 + 4) : n * 16;
         }
         if (mode == SEG_ACC_SET) x = n * 8;
@@ -437,7 +439,7 @@ static double op_bytes(const HostMesh &hm, Toucher &tch, const Op &op, int forci
         // SEG_INPLACE plus the sum read
         if (mode == SEG_RK_SET || mode == SEG_RK_ADD2) x = n * ((cell ? 3 : 2) * R + (mode == SEG_RK_SET ? 8 : 16));
         if (mode == SEG_RK_FIN) {
-            if (cell) x = fp32 ? n * (16 + 8 + 4 + 4 + 4 + 8) : n * (16 + 8 + 8);
+            if (cell) x = fp32 ? n * (16 + 4 + 4 + 4 + 8) : n * (16 + 8 + 8);
             else x = fp32 ? n * (16 + 4 + 8) : n * (16 + 8);
         }
         return x;
