@@ -383,9 +383,9 @@ fblts_status fblts_state_step_bytes(const fblts_state *state, double *alg_bytes,
  *              factors per edge and per cell; the same model as
  *              fblts_state_step_bytes and fblts_state_profile_step;
  *   moved[k] - what this library's kernels read and write in their layout:
- *              padded rows, 16-byte records, per-slot coefficients, and the
- *              per-slot shares that the FP32 path's TRiSK pass writes and its
- *              edge pass reads.
+ *              padded rows and records, per-slot coefficients, and the
+ *              shares that the FP32 path's TRiSK pass writes and its edge
+ *              pass reads.
  * moved / alg is the layout's overhead; DRAM traffic above moved means
  * re-reads that the caches did not catch. */
 fblts_status fblts_state_bytes_by_kind(const fblts_state *state, double *alg, double *moved);

@@ -311,8 +311,9 @@ FB_HD void prep32_body(const DevMesh &m, const PrepArgs32 &a, int e) {
 // gives s1, X = l u gives s_v.  The share of slot k is {t = q_{e_k} s0 + s1,
 // s_v} and the cell writes {B_i = K_i + g xi*_i (+ p_s / rho0), xi*_i} once,
 // so the edge pass forms Phi_e = [(t_0 + t_1)/2 - (B_c1 - B_c0)] / d_e from
-// one coalesced 16-byte load and the two cells' records.  q_{e_k} = (q at the two vertices of e_k) / 2: the
-// row's vertex k is the counter-clockwise end of e_k, vertex k-1 the other.
+// one coalesced 16-byte load and the two cells' records.  q_{e_k} = (q at the
+// two vertices of e_k) / 2: the row's vertex k is the counter-clockwise end
+// of e_k, vertex k-1 the other.
 // Rows are padded to S slots with valid indices; slots >= nEoC are masked.
 template <int S, bool VORTEX>
 FB_HD void trisk32_body(const DevMesh &m, const TriskArgs32 &a, const DevForcing &fz, int i) {

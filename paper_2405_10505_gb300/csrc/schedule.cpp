@@ -408,7 +408,7 @@ private:
 //     implementation only and count nothing: the math of Phi is counted where
 //     its inputs are read.
 //   moved - what the kernels of this library read and write: padded rows at
-//     their stored width, 16-byte records, per-slot coefficients and the
+//     their stored width, padded records, per-slot coefficients and the
 //     shares (written by the TRiSK pass, read by the edge pass).
 // FP32: stage data, kinetic energy, PV and coefficients in float; the time
 // level, 1/A and the correction sums in double.
