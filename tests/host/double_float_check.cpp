@@ -4,7 +4,11 @@
 //                 nearest, ties to even) bit for bit;
 //   df_add_prod - a sum of eight exact float products in double-float must
 //                 stay within 2^-44 of the largest term of the exact sum.
-// Prints "round <checked> <mismatches>" and "sum <checked> <worst error / 2^-46>".
+//   the FP64 path's double-float helpers (split, ten-term sums of products,
+//                 product, sum, square root, reciprocal) and the Newton
+//                 reciprocal in double, against long double.
+// Prints "round <checked> <mismatches>", "sum <checked> <worst error / 2^-46>"
+// and "fp64 <split> <sum10> <mul> <add> <sqrt> <rcp> <newton>" (relative errors).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -70,5 +74,39 @@ int main() {
         ++m;
     }
     std::printf("sum %ld %.6f\n", m, worst);
+
+    // the FP64 path's helpers against long double (relative errors)
+    std::uniform_real_distribution<double> D(0.5, 2.0);
+    std::uniform_int_distribution<int> X(-20, 20);
+    double e_split = 0, e_sum10 = 0, e_mul = 0, e_add = 0, e_sqrt = 0, e_rcp = 0, e_nr = 0;
+    for (int t = 0; t < 200000; ++t) {
+        const double a = std::ldexp(D(g), X(g)) * (t & 1 ? -1.0 : 1.0), b = std::ldexp(D(g), X(g));
+        const float2 sa = df_split(a), sb = df_split(b);
+        e_split = std::fmax(e_split, std::fabs(df_value(sa) - a) / std::fabs(a));
+        const long double pa = (long double)df_value(sa), pb = (long double)df_value(sb);
+        const float2 pm = ff_mul(sa, sb), ps = ff_add(sa, sb);
+        e_mul = std::fmax(e_mul, (double)(std::fabs((long double)df_value(pm) - pa * pb) / std::fabs(pa * pb)));
+        const long double exact_sum = pa + pb;
+        if (exact_sum != 0)   // relative to the larger operand (cancellation is exact in the leading parts)
+            e_add = std::fmax(e_add, (double)(std::fabs((long double)df_value(ps) - exact_sum) /
+                                              std::fmax(std::fabs(pa), std::fabs(pb))));
+        const float2 rt = ff_sqrt(sb), rc = ff_rcp(sb);
+        e_sqrt = std::fmax(e_sqrt, (double)(std::fabs((long double)df_value(rt) - std::sqrt(pb)) / std::sqrt(pb)));
+        e_rcp = std::fmax(e_rcp, (double)(std::fabs((long double)df_value(rc) - 1.0L / pb) * pb));
+        e_nr = std::fmax(e_nr, (double)(std::fabs((long double)rcp_nr(b) - 1.0L / (long double)b) * (long double)b));
+        // a ten-term sum of products, as in the edgesOnEdge sums
+        float2 s10 = make_float2(0.f, 0.f);
+        long double ex = 0.0L, big = 0.0L;
+        for (int j = 0; j < 10; ++j) {
+            const double w = std::ldexp(D(g), X(g) / 4) * (j & 1 ? -1.0 : 1.0), f = std::ldexp(D(g), X(g) / 4);
+            const float2 sw = df_split(w), sf = df_split(f);
+            df_fma(s10, sw, sf);
+            const long double p = (long double)df_value(sw) * (long double)df_value(sf);
+            ex += p;
+            big = std::fmax(big, std::fabs(p));
+        }
+        e_sum10 = std::fmax(e_sum10, (double)(std::fabs((long double)df_value(s10) - ex) / big));
+    }
+    std::printf("fp64 %.3e %.3e %.3e %.3e %.3e %.3e %.3e\n", e_split, e_sum10, e_mul, e_add, e_sqrt, e_rcp, e_nr);
     return 0;
 }
